@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of one stochastic-reconfiguration step of CNN-wavefunction VMC.
+
+A step is one pass of the whole hot path on one batch of synthetic input:
+Metropolis sampling (one sample per sweep per chain), local energies of every
+sample (connected-configuration enumeration, CNN forwards of all connected
+configurations, FP64 reduction), local derivatives O_k, the SR conjugate
+gradient to rtol 1e-8 and the parameter update.
+
+Default workload: J1-J2, 10x10 periodic lattice, J2 = 0.5, 6 conv layers of
+16 channels, 8192 samples over 256 chains (random-init parameters, synthetic
+data). value = E_loc samples/s of the tensor-core path; the plain FP32 path
+is measured in the same run for comparison.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = 'E_loc samples/s & SR steps/s vs plain FP32 path, same GB300; p50/p99 step latency'
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32', 'fp64'])
+    ap.add_argument('--workload', default='j1j2_10x10')
+    ap.add_argument('--compare-steps', type=int, default=2, help='steps of the plain FP32 path')
+    ap.add_argument('--oracle-samples', type=int, default=256, help='bounded sample for the CPU oracle')
+    return ap.parse_args()
+
+
+def dense_forward_flops(w):
+    N = w['L'] ** 2
+    fl = 0
+    for l in range(w['n_layers']):
+        cin = w['c_in'] if l == 0 else w['channels']
+        fl += 2 * 9 * cin * w['channels'] * N
+    return fl
+
+
+def load_peaks():
+    path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), 'measured'
+    return {'hbm_gbs': 6800.0, 'bf16_tflops': 1900.0, 'bf16_tflops_sustained': 1700.0, 'sm_max_mhz': 2070.0}, 'fallback'
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ('index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix='.csv')
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '--query-gpu=' + self.FIELDS, '--format=csv,noheader,nounits',
+                                          '-lms', '200', '-f', self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(',')]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and self.uuid not in parts[1]:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace('.', '').isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace('.', '').isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == 'active'})
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
+                'reasons': reasons, 'samples': len(rows)}
+
+
+# ------------------------------------------------------------------ oracle (CPU baseline, reference arm)
+def _oracle_chunk(args):
+    wname, params, cfg = args
+    import nqs_synth
+    from oracle import cnn, eloc, hamiltonian
+    w = nqs_synth.WORKLOADS[wname]
+    spec = cnn.NetSpec(w['L'], w['c_in'], w['channels'], w['n_layers'])
+    ham = (hamiltonian.J1J2(w['L'], w['J1'], w['J2']) if w['model'] == 'j1j2'
+           else hamiltonian.TJ(w['L'], w['t'], w['J']))
+    return eloc.local_energy(params, cfg, spec, ham)
+
+
+def oracle_eloc(wname, params, cfg, pool, cores):
+    chunks = [(wname, params, c) for c in _split(cfg, cores * 2)]
+    t0 = time.perf_counter()
+    parts = pool.map(_oracle_chunk, chunks)
+    dt = time.perf_counter() - t0
+    import numpy as np
+    return np.concatenate(parts), dt
+
+
+def _split(a, k):
+    n = a.shape[0]
+    step = max(1, (n + k - 1) // k)
+    return [a[i:i + step] for i in range(0, n, step)]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the machine's host cores, each step a
+    bounded sample of the same workload's E_loc."""
+    rank = int(os.environ.get('RANK', '0'))
+    if rank != 0:
+        return
+    import numpy as np
+    import nqs_synth
+    w = nqs_synth.WORKLOADS[args.workload]
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    cores = host_cores()
+    per_step = min(args.oracle_samples, 64)
+    ctx = mp.get_context('spawn')
+    with ctx.Pool(cores) as pool:
+        times = []
+        for k in range(args.warmup + args.steps):
+            cfg = nqs_synth.random_configs(w['L'] ** 2, w['n_up'], w['n_down'], per_step, seed=100 + k)
+            _, dt = oracle_eloc(args.workload, params, cfg, pool, cores)
+            if k >= args.warmup:
+                times.append(dt)
+    total = sum(times)
+    value = per_step * len(times) / total
+    line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'samples/s', 'n_gpus': 0,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1000 * total / len(times),
+            'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+            'data': 'synthetic', 'config': _config(w, args.workload, 'oracle'),
+            'cpu_baseline': {'value': value, 'unit': 'samples/s', 'cores': cores, 'kind': 'oracle',
+                             'sample': '%d uniform random sector configurations per step, E_loc only' % per_step},
+            'e2e': {'value': value, 'unit': 'samples/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(w, wname, precision):
+    return {'workload': '%s: %s %dx%d, %d conv layers x %d channels, %d samples / %d chains' % (
+        wname, 'J1-J2 (J2=0.5)' if w['model'] == 'j1j2' else 't-J (t=1, J=0.4)', w['L'], w['L'], w['n_layers'],
+        w['channels'], w['n_samples'], w['n_chains']),
+        'precision': precision, 'n_samples': w['n_samples'], 'n_chains': w['n_chains'],
+        'lattice': '%dx%d' % (w['L'], w['L']), 'sr': {'eps': 1e-4, 'rtol': 1e-8, 'lr': 0.02},
+        'l2': 'flushed (256 MB write) before every timed step', 'parallelism': 'replicas'}
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == 'reference':
+        run_reference(args)
+        return
+    # the oracle's process pool is started before the first GPU call
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    local_rank = int(os.environ.get('LOCAL_RANK', '0'))
+    cores = host_cores()
+    pool = mp.get_context('spawn').Pool(cores) if rank == 0 else None
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300 import nqs
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local_rank))
+    if rank == 0:
+        nbuild.build()
+    if world > 1:
+        dist.barrier()
+    nqs.load()
+
+    w = nqs_synth.WORKLOADS[args.workload]
+    dev = torch.device('cuda', local_rank)
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    if w['model'] == 'j1j2':
+        prob = nqs.make_problem('j1j2', w['L'], J1=w['J1'], J2=w['J2'], n_layers=w['n_layers'],
+                                channels=w['channels'])
+    else:
+        prob = nqs.make_problem('tj', w['L'], t=w['t'], J=w['J'], n_up=w['n_up'], n_down=w['n_down'],
+                                n_layers=w['n_layers'], channels=w['channels'])
+    n_chains, n_samples = w['n_chains'], w['n_samples']
+    spc = n_samples // n_chains
+    P = nqs.nqs_param_count(prob)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def new_ctx(seed):
+        tp = torch.tensor(params, dtype=torch.float64, device=dev)
+        return nqs.Context(prob, tp, seed=seed + 1000 * rank)
+
+    def sr_step(ctx, prec, ev, burn=0):
+        ev[0].record(stream)
+        cfg, lp = ctx.sample(n_chains, spc, 1, burn, prec)
+        ev[1].record(stream)
+        e = ctx.local_energy(cfg, None, prec)
+        ev[2].record(stream)
+        O = ctx.logpsi_grad(cfg, prec)
+        ev[3].record(stream)
+        _, info = ctx.sr_solve(O, e, eps=1e-4, rtol=1e-8, max_iter=min(P, 10000), lr=0.02, apply_update=True)
+        ev[4].record(stream)
+        return cfg, e, info
+
+    def run(prec, steps, warmup, sampler_clock=None):
+        ctx = new_ctx(7)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        wev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        sr_step(ctx, prec, wev, burn=10)
+        for _ in range(max(0, warmup - 1)):
+            sr_step(ctx, prec, wev)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler_clock:
+            sampler_clock.start()
+        l0 = ctx.kernel_launches()
+        infos = []
+        last = None
+        for k in range(steps):
+            flush.zero_()
+            last = sr_step(ctx, prec, evs[k])
+            infos.append(last[2])
+        torch.cuda.synchronize()
+        launches = ctx.kernel_launches() - l0
+        clocks = sampler_clock.stop() if sampler_clock else None
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(steps)])
+        return ctx, stage, infos, launches, clocks, last
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clock = ClockSampler(uuid)
+    ctx, stage, infos, launches, clocks, last = run(args.precision, args.steps, args.warmup, clock)
+    step_ms = stage.sum(axis=1)
+    eloc_ms = stage[:, 1]
+    # max over ranks of the timed totals
+    tot = torch.tensor([eloc_ms.sum(), step_ms.sum()], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    eloc_total_ms, step_total_ms = tot.tolist()
+    value = n_samples * args.steps * world / (eloc_total_ms / 1000.0)
+    sr_steps_per_s = args.steps * world / (step_total_ms / 1000.0)
+
+    # algorithmic FLOPs of one E_loc launch: (n_c + 1) dense forwards per sample
+    cfg_last, e_last, _ = last
+    n_conn = ctx.connected(cfg_last)[0].to(torch.int64).sum().item()
+    flops = (n_conn + n_samples) * dense_forward_flops(w)
+
+    # E_loc through the public API with host buffers (copies inside the timed region)
+    cfg_host = cfg_last.cpu().pin_memory()
+    out_host = torch.empty((n_samples, 2), dtype=torch.float64).pin_memory()
+    cfg_dev = torch.empty_like(cfg_last)
+    for _ in range(2):
+        cfg_dev.copy_(cfg_host, non_blocking=True)
+        out_host.copy_(ctx.local_energy(cfg_dev, None, args.precision), non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        cfg_dev.copy_(cfg_host, non_blocking=True)
+        out_host.copy_(ctx.local_energy(cfg_dev, None, args.precision), non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = n_samples * args.steps * world / (e0.elapsed_time(e1) / 1000.0)
+
+    # energy check: this path against the FP64 GPU path (all samples) and the oracle (bounded subset)
+    e_fp64 = ctx.local_energy(cfg_last, None, 'fp64').cpu().numpy()
+    e_this = ctx.local_energy(cfg_last, None, args.precision).cpu().numpy()
+    N = w['L'] ** 2
+    check = {'energy_per_site_vs_fp64_gpu': abs(e_this[:, 0].mean() - e_fp64[:, 0].mean()) / N,
+             'max_abs_eloc_diff_vs_fp64_gpu': float(np.abs(e_this[:, 0] - e_fp64[:, 0]).max())}
+
+    # plain FP32 path on the same workload
+    cmp = None
+    if args.compare_steps > 0 and args.precision != 'fp32':
+        ctx32, st32, inf32, _, _, _ = run('fp32', args.compare_steps, 1)
+        cmp = {'eloc_samples_per_s': n_samples * args.compare_steps / (st32[:, 1].sum() / 1000.0),
+               'sr_steps_per_s': args.compare_steps / (st32.sum() / 1000.0),
+               'ms_per_step': float(st32.sum(axis=1).mean()), 'eloc_ms': float(st32[:, 1].mean())}
+        ctx32.close()
+
+    line = None
+    if rank == 0:
+        peaks, peak_kind = load_peaks()
+        eloc_launch_s = float(eloc_ms.mean()) / 1000.0
+        achieved = flops / eloc_launch_s / 1e12
+        if args.precision == 'bf16':
+            peak = peaks.get('bf16_tflops_sustained') or peaks['bf16_tflops']
+            roof = {'bound': 'tensor', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s',
+                    'frac': achieved / peak, 'traffic': None, 'kernel': 'eloc_tc_kernel',
+                    'peak_source': '%s bf16 dense (sustained)' % peak_kind}
+        else:
+            mhz = (clocks or {}).get('sm_mhz') or peaks.get('sm_max_mhz', 2070.0)
+            lanes = 128 if args.precision == 'fp32' else 2
+            peak = 152 * lanes * 2 * mhz * 1e6 / 1e12
+            roof = {'bound': 'alu', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s', 'frac': achieved / peak,
+                    'traffic': None, 'kernel': 'eloc_plain_kernel',
+                    'peak_source': '152 SMs x %d lanes x 2 FLOP x %.0f MHz' % (lanes, mhz)}
+        # CPU oracle on a bounded sample of the same workload
+        sub = cfg_last[:args.oracle_samples].cpu().numpy()
+        e_or, dt_or = oracle_eloc(args.workload, params_at_step(ctx), sub, pool, cores)
+        e_sub = ctx.local_energy(cfg_last[:args.oracle_samples], None, args.precision).cpu().numpy()
+        check['energy_per_site_vs_oracle_subset'] = abs(e_sub[:, 0].mean() - e_or.real.mean()) / N
+        check['oracle_subset_samples'] = int(sub.shape[0])
+        line = {
+            'metric': METRIC, 'value': value, 'unit': 'samples/s', 'n_gpus': world, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': float(step_total_ms / args.steps), 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': args.precision, 'data': 'synthetic',
+            'config': _config(w, args.workload, args.precision),
+            'sr_steps_per_s': sr_steps_per_s,
+            'latency_ms': {'p50': float(np.percentile(step_ms, 50)), 'p99': float(np.percentile(step_ms, 99))},
+            'stage_ms': {k: float(stage[:, i].mean()) for i, k in enumerate(['sample', 'eloc', 'grad', 'sr'])},
+            'cg_iters': [int(i['iters']) for i in infos],
+            'energy_per_site': float(e_last[:, 0].mean().item()) / N,
+            'vs_plain_fp32': cmp,
+            'energy_check': check,
+            'roofline': roof,
+            'cpu_baseline': {'value': sub.shape[0] / dt_or, 'unit': 'samples/s', 'cores': cores, 'kind': 'oracle',
+                             'sample': '%d of the step\'s samples, E_loc only (FP64 numpy oracle, spawn pool)' %
+                                       sub.shape[0]},
+            'e2e': {'value': e2e_value, 'unit': 'samples/s', 'h2d_bytes_per_step': int(cfg_host.numel()),
+                    'd2h_bytes_per_step': int(out_host.numel() * 8),
+                    'what': 'nqs_local_energy on host configs: H2D copy + E_loc + D2H of E_loc per step'},
+            'gpu_launches': int(launches),
+            'clocks': clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pool is not None:
+        pool.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def params_at_step(ctx):
+    return ctx.params.detach().cpu().numpy().copy()
+
+
+if __name__ == '__main__':
+    main()

@@ -1,0 +1,193 @@
+/*
+ * nqs.h - C ABI of the GB300 (sm_103a) library for the hot path of
+ * CNN-wavefunction variational Monte Carlo (arXiv 2204.07816).
+ *
+ * The library evaluates, for a convolutional wave function
+ * W(S) = exp(a(S) + i phi(S)) (Eq. 1 of the paper), the quantities of one
+ * stochastic-reconfiguration step of the self-learning procedure (Sec. 3.2):
+ * MCMC samples drawn from |W(S)|^2, local energies E_loc (Sec. 5.4.1,
+ * "Hotspot energy calculation"), local derivatives O_loc = d log W / d theta,
+ * and the SR solve and parameter update (Sec. 5.4.1, "Distributed SR
+ * computation"). Hamiltonians: J1-J2 (Eq. 2) and t-J (Eq. 3) on an L x L
+ * periodic square lattice.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Sites: (x, y), 0 <= x, y < L, index y*L + x. N = L*L.
+ * - Site values (int8): J1-J2 +1 = up, -1 = down; t-J 0 = hole, +1 = up,
+ *   -1 = down.
+ * - Network: n_layers x [3x3 periodic convolution + bias, SiLU], input one
+ *   channel (the site value) for J1-J2 and three one-hot channels
+ *   (hole, up, down) for t-J; head a = w_a . sum_sites h, phi = w_phi . sum_sites h.
+ * - Parameters: one float64 vector, per layer W[C_out][C_in][3][3] then
+ *   b[C_out], then w_a[C], w_phi[C]. Its length is nqs_param_count().
+ * - log psi arrays are [n][2] float64 rows (a, phi); local energies are
+ *   [n][2] float64 rows (Re E_loc, Im E_loc).
+ * - Every array argument is a DEVICE pointer owned by the caller, unless a
+ *   comment says otherwise. The library owns the context, the Markov chain
+ *   state, the Philox counters and its workspace.
+ * - Every call is enqueued on the stream given to nqs_init and returns once
+ *   the work is enqueued; the outputs are valid after the stream has
+ *   reached that point (nqs_sync waits for it). Argument errors are
+ *   returned at once. Errors that the GPU finds (a non-finite value, a wait
+ *   that ran out of iterations) are latched in the context and returned by
+ *   the next nqs_sync.
+ * - Return values: NQS_OK or a negative nqs_status. On error the outputs
+ *   are unspecified and the chain state is unchanged. nqs_last_error gives
+ *   a one-line description.
+ * - Precisions: NQS_FP64 and NQS_FP32 run the convolutions on CUDA cores in
+ *   that type; NQS_BF16 runs them on the tcgen05 tensor cores with bf16
+ *   operands and fp32 accumulation in tensor memory. In every precision the
+ *   log-amplitude ratios, E_loc, energies and the SR solve are float64.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nqs_ctx nqs_ctx;
+
+typedef enum {
+    NQS_OK = 0,
+    NQS_ERR_INVALID_ARG = -1,
+    NQS_ERR_OOM = -2,
+    NQS_ERR_CUDA = -3,
+    NQS_ERR_NONFINITE = -4,
+    NQS_ERR_NOT_CONVERGED = -5,
+    NQS_ERR_TIMEOUT = -6,
+    NQS_ERR_UNSUPPORTED = -7
+} nqs_status;
+
+typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_BF16 = 2 } nqs_precision;
+
+typedef enum { NQS_MODEL_J1J2 = 0, NQS_MODEL_TJ = 1 } nqs_model;
+
+/* The physical problem and the network shape. Eq. 2 uses J1, J2 and
+ * sign_rule; Eq. 3 uses t and J. n_up / n_down fix the sector the sampler
+ * draws from (J1-J2: n_up + n_down = N; t-J: holes = N - n_up - n_down).
+ * sign_rule (J1-J2 only, 0 or 1) multiplies the basis by
+ * (-1)^(up spins on the (x+y)-even sublattice), which flips the sign of the
+ * nearest-neighbour exchange elements. */
+typedef struct {
+    int32_t model;      /* nqs_model */
+    int32_t L;          /* 4 <= L <= 36 */
+    double J1, J2;      /* J1-J2 couplings */
+    double t, J;        /* t-J couplings */
+    int32_t n_up, n_down;
+    int32_t sign_rule;
+    int32_t n_layers;   /* >= 1 */
+    int32_t channels;   /* 4, 8, 16 or 32 */
+} nqs_problem;
+
+/* Number of network parameters for problem p (layout above); -1 if p is
+ * invalid. Host only, no GPU work. */
+int64_t nqs_param_count(const nqs_problem *p);
+
+/* Create a context on the current CUDA device.
+ * params: device float64 [nqs_param_count(p)], caller-owned and borrowed
+ *   for the life of the context; the library reads it at every call (so
+ *   the caller may change it between calls) and nqs_sr_solve with
+ *   apply_update = 1 writes it in place.
+ * seed: Philox key for the sampler (Sec. 3.2 MCMC): proposals use key
+ *   (seed, 0), initial chain states key (seed, 1).
+ * stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Returns NQS_ERR_INVALID_ARG for a bad problem, NQS_ERR_CUDA if no
+ * sm_100-family device is current. */
+int nqs_init(nqs_ctx **out, const nqs_problem *p, double *params, uint64_t seed, void *stream);
+
+/* Wait for the context's stream and frees every resource. Returns the
+ * latched device error, if any. */
+int nqs_destroy(nqs_ctx *ctx);
+
+/* One-line description of the last error of this context (static string if
+ * ctx is NULL). Host memory owned by the library. */
+const char *nqs_last_error(const nqs_ctx *ctx);
+
+/* Wait for the context's stream; return and clear the latched device error. */
+int nqs_sync(nqs_ctx *ctx);
+
+/* Number of GPU kernels this context has launched so far (a monotone
+ * counter for accounting; -1 if ctx is NULL). Host only. */
+int64_t nqs_kernel_launches(const nqs_ctx *ctx);
+
+/* log psi of n configurations (Eq. 1: the network's log-amplitude and
+ * phase). configs: device int8 [n][N]; logpsi_out: device float64 [n][2]. */
+int nqs_logpsi(nqs_ctx *ctx, const int8_t *configs, int64_t n, double *logpsi_out, int32_t precision);
+
+/* Connected configurations (Sec. 5.4.1 "sprime_batch"; matrix elements of
+ * Eq. 2 or Eq. 3). For sample s, the bonds that change configs[s] are
+ * listed in bond order: site-major, then direction (x+1), (y+1), and for
+ * J1-J2 also (x+1, y+1), (x+1, y-1). Entry k of sample s:
+ *   pairs_out[s][k] = (i, j) (int32 x2), the swapped sites,
+ *   h_out[s][k]     = <S|H|S'> (float64),
+ * n_conn_out[s] = number of entries, hdiag_out[s] = <S|H|S> (float64).
+ * Every output array is a device array sized for max_conn entries per
+ * sample (max_conn >= 4N for J1-J2, >= 2N for t-J). Integer outputs and the
+ * off-diagonal values are exact. */
+int nqs_connected(nqs_ctx *ctx, const int8_t *configs, int64_t n, int32_t max_conn,
+                  int32_t *n_conn_out, int32_t *pairs_out, double *h_out, double *hdiag_out);
+
+/* Local energies (Sec. 5.4.1: E_loc(S) = sum_S' W(S')/W(S) <S'|H|S>):
+ * eloc_out[s] = H_SS + sum_k H_k exp((a'_k - a) + i (phi'_k - phi)).
+ * configs: device int8 [n][N]. logpsi: device float64 [n][2] giving
+ * (a, phi) of each configuration, or NULL to have the library recompute it
+ * with the same precision as the connected configurations (recommended for
+ * NQS_BF16, so that the rounding of numerator and denominator matches).
+ * eloc_out: device float64 [n][2]. */
+int nqs_local_energy(nqs_ctx *ctx, const int8_t *configs, const double *logpsi, int64_t n,
+                     double *eloc_out, int32_t precision);
+
+/* Metropolis exchange sampling from |W(S)|^2 (Sec. 3.2; Sec. 5.4.1
+ * "Process-level / thread-level parallel MCMC": many independent chains).
+ * The context keeps n_chains chains on the device across calls; the first
+ * call (or a call with a different n_chains) starts them from Fisher-Yates
+ * shuffles of the sector's site values. Proposal number s of chain c uses
+ * Philox4x64-10 block (c, s, 0, 0) under key (seed, 0): site
+ * i = floor(B0 N / 2^64), neighbour direction B1 >> 62 (x+1, x-1, y+1, y-1),
+ * u = (B2 >> 11) 2^-53; it swaps i and j when their values differ and is
+ * accepted iff 2(a' - a) >= 0 or u < exp(2(a' - a)). burn_in sweeps of N
+ * proposals are discarded, then a sample is kept after every
+ * sweeps_between-th sweep. configs_out: device int8
+ * [n_chains * samples_per_chain][N], chain-major; logpsi_out: device
+ * float64 [same][2]. */
+int nqs_sample(nqs_ctx *ctx, int32_t n_chains, int32_t samples_per_chain, int32_t sweeps_between,
+               int32_t burn_in, int8_t *configs_out, double *logpsi_out, int32_t precision);
+
+/* Chain checkpoint / resume. chains: device int8 [n_chains][N]; step: host
+ * uint64, the number of proposals every chain has made. get copies the
+ * current state out (n_chains must match the context's); set replaces it
+ * (the log-amplitudes are recomputed at the next nqs_sample). */
+int nqs_get_chains(nqs_ctx *ctx, int32_t n_chains, int8_t *chains, uint64_t *step);
+int nqs_set_chains(nqs_ctx *ctx, int32_t n_chains, const int8_t *chains, uint64_t step);
+
+/* Local derivatives O_loc (Sec. 3.2: the backward of the network gives
+ * O_loc), real-stacked: O_out is device float64 [2n][P] with row s equal to
+ * d a(S_s)/d theta and row n + s equal to d phi(S_s)/d theta, so that
+ * O_k = row s + i * row (n + s). */
+int nqs_logpsi_grad(nqs_ctx *ctx, const int8_t *configs, int64_t n, double *O_out, int32_t precision);
+
+/* Stochastic reconfiguration (Sec. 3.2; Sec. 5.4.1 "Distributed SR
+ * computation", solved here matrix-free by conjugate gradient):
+ *   <E> = mean E_loc, Oc = O - mean O,
+ *   S = Re(Oc^H Oc)/n, F = Re(Oc^H (E_loc - <E>))/n,
+ *   (S + eps I) delta = F by CG from delta = 0 until ||r|| <= rtol ||F||
+ *   or max_iter iterations, then theta <- theta - lr delta if apply_update.
+ * O: device float64 [2n][P] as written by nqs_logpsi_grad; eloc: device
+ * float64 [n][2]; delta_out: device float64 [P]. iters_out, resid_out
+ * (relative residual) and energy_out ([2]: Re, Im of <E>) are HOST
+ * pointers, written before the call returns (the call waits for the
+ * stream). Returns NQS_ERR_NOT_CONVERGED (delta and the update still
+ * applied) when max_iter is reached first. */
+int nqs_sr_solve(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, double eps, double rtol,
+                 int32_t max_iter, double lr, double *delta_out, int32_t *iters_out, double *resid_out,
+                 double *energy_out, int32_t apply_update);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NQS_H */

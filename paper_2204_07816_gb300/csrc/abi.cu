@@ -1,0 +1,348 @@
+// C ABI of the library (declared in include/nqs.h): context lifetime,
+// argument validation, workspace and chain-state ownership, dispatch to the
+// CUDA-core and tensor-core kernels.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+using namespace nqs;
+
+struct nqs_ctx {
+    Problem p;
+    nqs_problem spec;
+    double *params = nullptr;      // borrowed
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    size_t max_smem = 0;
+    int *err_dev = nullptr;        // device error bits
+    float *params32 = nullptr;     // float copy for the FP32 path
+    void *packed = nullptr;        // tensor-core operand images
+    int8_t *chains = nullptr;
+    int n_chains = 0;
+    uint64_t step = 0;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int64_t launches = 0;
+    std::string msg;
+};
+
+namespace {
+
+const char *kNoCtx = "no context";
+thread_local std::string g_init_error;
+
+int fail(nqs_ctx *c, int code, const std::string &m) {
+    if (c) c->msg = m;
+    return code;
+}
+
+int cuda_fail(nqs_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? NQS_ERR_OOM : NQS_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_problem(const nqs_problem *q, std::string *why) {
+    if (!q) { *why = "problem is NULL"; return false; }
+    if (q->model != NQS_MODEL_J1J2 && q->model != NQS_MODEL_TJ) { *why = "model must be 0 (J1-J2) or 1 (t-J)"; return false; }
+    if (q->L < 4 || q->L > 36) { *why = "L must be in [4, 36]"; return false; }
+    if (q->n_layers < 1 || q->n_layers > 16) { *why = "n_layers must be in [1, 16]"; return false; }
+    if (q->channels != 4 && q->channels != 8 && q->channels != 16 && q->channels != 32) {
+        *why = "channels must be 4, 8, 16 or 32";
+        return false;
+    }
+    const int N = q->L * q->L;
+    if (q->n_up < 0 || q->n_down < 0 || q->n_up + q->n_down > N) { *why = "bad n_up / n_down"; return false; }
+    if (q->model == NQS_MODEL_J1J2 && q->n_up + q->n_down != N) { *why = "J1-J2 needs n_up + n_down = L*L"; return false; }
+    if (q->sign_rule != 0 && q->sign_rule != 1) { *why = "sign_rule must be 0 or 1"; return false; }
+    if (q->sign_rule && q->model != NQS_MODEL_J1J2) { *why = "sign_rule applies to J1-J2 only"; return false; }
+    return true;
+}
+
+Problem make_problem(const nqs_problem *q) {
+    Problem p;
+    p.model = q->model;
+    p.L = q->L;
+    p.N = q->L * q->L;
+    p.c_in = q->model == NQS_MODEL_J1J2 ? 1 : 3;
+    p.C = q->channels;
+    p.n_layers = q->n_layers;
+    p.J1 = q->J1; p.J2 = q->J2; p.t = q->t; p.J = q->J;
+    p.sign_rule = q->sign_rule;
+    p.P = (9 * p.c_in * p.C + p.C) + (p.n_layers - 1) * (9 * p.C * p.C + p.C) + 2 * p.C;
+    p.n_bonds = (q->model == NQS_MODEL_J1J2 ? 4 : 2) * p.N;
+    p.n_up = q->n_up;
+    p.n_down = q->n_down;
+    return p;
+}
+
+LaunchEnv env_of(nqs_ctx *c) {
+    LaunchEnv e;
+    e.stream = c->stream;
+    e.num_sms = c->num_sms;
+    e.max_smem = c->max_smem;
+    e.err = c->err_dev;
+    e.launches = &c->launches;
+    e.msg = &c->msg;
+    return e;
+}
+
+bool valid_precision(int prec) { return prec == NQS_FP64 || prec == NQS_FP32 || prec == NQS_BF16; }
+
+// Prepare the parameter image a precision needs (read from the caller's
+// float64 vector on every call, so caller-side changes are always seen).
+int prepare_params(nqs_ctx *c, int prec, DeviceParams *dp) {
+    dp->p64 = c->params;
+    dp->p32 = c->params32;
+    if (prec == NQS_FP32) {
+        launch_convert_params(c->params, c->params32, c->p.P, c->stream);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "convert params");
+        ++c->launches;
+    } else if (prec == NQS_BF16) {
+        LaunchEnv env = env_of(c);
+        int rc = launch_tc_pack(c->p, c->params, c->packed, env);
+        if (rc) return rc;
+    }
+    return NQS_OK;
+}
+
+int ensure_scratch(nqs_ctx *c, size_t bytes) {
+    if (bytes <= c->scratch_bytes) return NQS_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream sync");
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    e = cudaMalloc(&c->scratch, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "workspace allocation");
+    c->scratch_bytes = bytes;
+    return NQS_OK;
+}
+
+int check_ctx(nqs_ctx *c) {
+    if (!c) return NQS_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return NQS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t nqs_param_count(const nqs_problem *q) {
+    std::string why;
+    if (!valid_problem(q, &why)) return -1;
+    return make_problem(q).P;
+}
+
+int nqs_init(nqs_ctx **out, const nqs_problem *q, double *params, uint64_t seed, void *stream) {
+    if (!out) return NQS_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string why;
+    if (!valid_problem(q, &why)) { g_init_error = why; return NQS_ERR_INVALID_ARG; }
+    if (!params) { g_init_error = "params is NULL"; return NQS_ERR_INVALID_ARG; }
+    nqs_ctx *c = new nqs_ctx();
+    c->spec = *q;
+    c->p = make_problem(q);
+    c->params = params;
+    c->seed = seed;
+    c->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) { g_init_error = cudaGetErrorString(e); delete c; return NQS_ERR_CUDA; }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, c->device);
+    if (e != cudaSuccess) { g_init_error = cudaGetErrorString(e); delete c; return NQS_ERR_CUDA; }
+    if (prop.major != 10) {
+        g_init_error = "needs a Blackwell (sm_10x) GPU";
+        delete c;
+        return NQS_ERR_CUDA;
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->max_smem = prop.sharedMemPerBlockOptin;
+    e = cudaMalloc(&c->err_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->params32, sizeof(float) * c->p.P);
+    if (e == cudaSuccess) {
+        const size_t pk = tc_packed_bytes(c->p);
+        e = cudaMalloc(&c->packed, pk ? pk : 16);
+    }
+    if (e != cudaSuccess) {
+        g_init_error = std::string("allocation: ") + cudaGetErrorString(e);
+        nqs_destroy(c);
+        return e == cudaErrorMemoryAllocation ? NQS_ERR_OOM : NQS_ERR_CUDA;
+    }
+    *out = c;
+    return NQS_OK;
+}
+
+int nqs_sync(nqs_ctx *c) {
+    if (int rc = check_ctx(c)) return rc;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    int bits = 0;
+    e = cudaMemcpy(&bits, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "error flag");
+    if (bits) {
+        cudaMemset(c->err_dev, 0, sizeof(int));
+        if (bits & ERRBIT_NONFINITE) return fail(c, NQS_ERR_NONFINITE, "a kernel produced a non-finite value");
+        if (bits & ERRBIT_TIMEOUT) return fail(c, NQS_ERR_TIMEOUT, "a device-side wait ran out of iterations");
+        return fail(c, NQS_ERR_CUDA, "a device-side bounds check failed");
+    }
+    return NQS_OK;
+}
+
+int nqs_destroy(nqs_ctx *c) {
+    if (!c) return NQS_ERR_INVALID_ARG;
+    int rc = nqs_sync(c);
+    cudaFree(c->err_dev);
+    cudaFree(c->params32);
+    cudaFree(c->packed);
+    cudaFree(c->chains);
+    cudaFree(c->scratch);
+    delete c;
+    return rc;
+}
+
+int64_t nqs_kernel_launches(const nqs_ctx *c) { return c ? c->launches : -1; }
+
+const char *nqs_last_error(const nqs_ctx *c) {
+    if (!c) return g_init_error.empty() ? kNoCtx : g_init_error.c_str();
+    return c->msg.c_str();
+}
+
+int nqs_logpsi(nqs_ctx *c, const int8_t *configs, int64_t n, double *out, int32_t prec) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0 || (n > 0 && (!configs || !out))) return fail(c, NQS_ERR_INVALID_ARG, "nqs_logpsi: bad arrays");
+    if (!valid_precision(prec)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_logpsi: bad precision");
+    if (n == 0) return NQS_OK;
+    DeviceParams dp;
+    if (int rc = prepare_params(c, prec, &dp)) return rc;
+    LaunchEnv env = env_of(c);
+    if (prec == NQS_BF16) return launch_logpsi_tc(c->p, c->params, c->packed, configs, n, out, env);
+    return launch_logpsi_plain(c->p, prec, dp, configs, n, out, env);
+}
+
+int nqs_connected(nqs_ctx *c, const int8_t *configs, int64_t n, int32_t max_conn, int32_t *n_conn,
+                  int32_t *pairs, double *h, double *hdiag) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0 || (n > 0 && (!configs || !n_conn || !pairs || !h || !hdiag)))
+        return fail(c, NQS_ERR_INVALID_ARG, "nqs_connected: bad arrays");
+    if (max_conn < c->p.n_bonds) return fail(c, NQS_ERR_INVALID_ARG, "nqs_connected: max_conn below the bond count");
+    LaunchEnv env = env_of(c);
+    return launch_connected(c->p, configs, n, max_conn, n_conn, pairs, h, hdiag, env);
+}
+
+int nqs_local_energy(nqs_ctx *c, const int8_t *configs, const double *logpsi, int64_t n, double *out, int32_t prec) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0 || (n > 0 && (!configs || !out))) return fail(c, NQS_ERR_INVALID_ARG, "nqs_local_energy: bad arrays");
+    if (!valid_precision(prec)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_local_energy: bad precision");
+    if (n == 0) return NQS_OK;
+    DeviceParams dp;
+    if (int rc = prepare_params(c, prec, &dp)) return rc;
+    LaunchEnv env = env_of(c);
+    if (prec == NQS_BF16) return launch_eloc_tc(c->p, c->params, c->packed, configs, logpsi, n, out, env);
+    return launch_eloc_plain(c->p, prec, dp, configs, logpsi, n, out, env);
+}
+
+int nqs_sample(nqs_ctx *c, int32_t n_chains, int32_t spc, int32_t sweeps_between, int32_t burn_in, int8_t *configs_out,
+               double *logpsi_out, int32_t prec) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n_chains <= 0 || spc < 0 || sweeps_between < 1 || burn_in < 0)
+        return fail(c, NQS_ERR_INVALID_ARG, "nqs_sample: bad counts");
+    if (spc > 0 && (!configs_out || !logpsi_out)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sample: bad arrays");
+    if (!valid_precision(prec)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sample: bad precision");
+    LaunchEnv env = env_of(c);
+    if (n_chains != c->n_chains || !c->chains) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream sync");
+        cudaFree(c->chains);
+        c->chains = nullptr;
+        c->n_chains = 0;
+        e = cudaMalloc(&c->chains, (size_t)n_chains * c->p.N);
+        if (e != cudaSuccess) return cuda_fail(c, e, "chain allocation");
+        if (int rc = launch_init_chains(c->p, c->seed, n_chains, c->chains, env)) return rc;
+        c->n_chains = n_chains;
+        c->step = 0;
+    }
+    DeviceParams dp;
+    if (int rc = prepare_params(c, prec, &dp)) return rc;
+    int rc;
+    if (prec == NQS_BF16)
+        rc = launch_sample_tc(c->p, c->params, c->packed, c->chains, n_chains, c->step, c->seed, spc, sweeps_between,
+                              burn_in, configs_out, logpsi_out, env);
+    else
+        rc = launch_sample_plain(c->p, prec, dp, c->chains, n_chains, c->step, c->seed, spc, sweeps_between, burn_in,
+                                 configs_out, logpsi_out, env);
+    if (rc) return rc;
+    c->step += (uint64_t)(burn_in + (int64_t)spc * sweeps_between) * c->p.N;
+    return NQS_OK;
+}
+
+int nqs_get_chains(nqs_ctx *c, int32_t n_chains, int8_t *chains, uint64_t *step) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n_chains != c->n_chains || !c->chains || !chains || !step)
+        return fail(c, NQS_ERR_INVALID_ARG, "nqs_get_chains: no chains of that size");
+    cudaError_t e = cudaMemcpyAsync(chains, c->chains, (size_t)n_chains * c->p.N, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "chain copy");
+    *step = c->step;
+    return NQS_OK;
+}
+
+int nqs_set_chains(nqs_ctx *c, int32_t n_chains, const int8_t *chains, uint64_t step) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n_chains <= 0 || !chains) return fail(c, NQS_ERR_INVALID_ARG, "nqs_set_chains: bad arguments");
+    if (n_chains != c->n_chains) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream sync");
+        cudaFree(c->chains);
+        c->chains = nullptr;
+        c->n_chains = 0;
+        e = cudaMalloc(&c->chains, (size_t)n_chains * c->p.N);
+        if (e != cudaSuccess) return cuda_fail(c, e, "chain allocation");
+        c->n_chains = n_chains;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->chains, chains, (size_t)n_chains * c->p.N, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "chain copy");
+    c->step = step;
+    return NQS_OK;
+}
+
+int nqs_logpsi_grad(nqs_ctx *c, const int8_t *configs, int64_t n, double *O, int32_t prec) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0 || (n > 0 && (!configs || !O))) return fail(c, NQS_ERR_INVALID_ARG, "nqs_logpsi_grad: bad arrays");
+    if (!valid_precision(prec)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_logpsi_grad: bad precision");
+    if (n == 0) return NQS_OK;
+    // the tensor-core precision differentiates with float32 internals
+    const int gp = prec == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    DeviceParams dp;
+    if (int rc = prepare_params(c, gp, &dp)) return rc;
+    const int blocks = (int)std::min<int64_t>(n, (int64_t)c->num_sms * 2);
+    if (int rc = ensure_scratch(c, grad_scratch_bytes(c->p, gp, blocks))) return rc;
+    LaunchEnv env = env_of(c);
+    return launch_grad_plain(c->p, gp, dp, configs, n, O, c->scratch, c->scratch_bytes, env);
+}
+
+int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, double eps, double rtol,
+                 int32_t max_iter, double lr, double *delta, int32_t *iters_out, double *resid_out,
+                 double *energy_out, int32_t apply_update) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n <= 0 || !O || !eloc || !delta) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve: bad arrays");
+    if (!(eps >= 0.0) || !(rtol >= 0.0) || max_iter < 0) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve: bad eps/rtol/max_iter");
+    if (int rc = ensure_scratch(c, sr_workspace_doubles(n, c->p.P) * sizeof(double))) return rc;
+    LaunchEnv env = env_of(c);
+    int iters = 0;
+    double resid = 0.0, energy[2] = {0.0, 0.0};
+    const int rc = run_sr_solve(c->p, O, eloc, n, eps, rtol, max_iter, lr, delta, c->params, apply_update,
+                                (double *)c->scratch, &iters, &resid, energy, env);
+    if (iters_out) *iters_out = iters;
+    if (resid_out) *resid_out = resid;
+    if (energy_out) { energy_out[0] = energy[0]; energy_out[1] = energy[1]; }
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Host-side interface between the C ABI (abi.cu) and the kernel files.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace nqs {
+
+struct LaunchEnv {
+    cudaStream_t stream;
+    int num_sms;
+    size_t max_smem;     // opt-in shared memory per block
+    int *err;            // device error bits
+    int64_t *launches;   // kernels launched so far by this context
+    std::string *msg;    // host error text
+};
+
+// Parameters converted for a precision: T = float copies of the layer
+// weights (FP32 path) or the packed bf16 operand images (tensor-core path).
+struct DeviceParams {
+    const double *p64;    // caller's float64 vector
+    const float *p32;     // float copy (same layout)
+};
+
+// ---- plain CUDA-core path (plain.cu); prec = NQS_FP64 or NQS_FP32
+int plain_max_group(const Problem &p, int prec, size_t extra_smem, size_t max_smem);
+int launch_logpsi_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
+                        double *out, const LaunchEnv &env);
+int launch_eloc_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs,
+                      const double *logpsi, int64_t n, double *out, const LaunchEnv &env);
+int launch_connected(const Problem &p, const int8_t *configs, int64_t n, int max_conn, int32_t *n_conn,
+                     int32_t *pairs, double *h, double *hdiag, const LaunchEnv &env);
+int launch_init_chains(const Problem &p, uint64_t seed, int n_chains, int8_t *chains, const LaunchEnv &env);
+int launch_sample_plain(const Problem &p, int prec, const DeviceParams &dp, int8_t *chains, int n_chains,
+                        uint64_t step0, uint64_t seed, int spc, int sweeps_between, int burn_in, int8_t *out_cfg,
+                        double *out_logpsi, const LaunchEnv &env);
+int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
+                      double *O, void *scratch, size_t scratch_bytes, const LaunchEnv &env);
+size_t grad_scratch_bytes(const Problem &p, int prec, int num_blocks);
+void launch_convert_params(const double *p64, float *p32, int P, cudaStream_t s);
+
+// ---- tensor-core path (tc.cu)
+bool tc_supported(const Problem &p, std::string *why);
+size_t tc_packed_bytes(const Problem &p);
+int launch_tc_pack(const Problem &p, const double *p64, void *packed, const LaunchEnv &env);
+int launch_logpsi_tc(const Problem &p, const double *p64, const void *packed, const int8_t *configs, int64_t n,
+                     double *out, const LaunchEnv &env);
+int launch_eloc_tc(const Problem &p, const double *p64, const void *packed, const int8_t *configs,
+                   const double *logpsi, int64_t n, double *out, const LaunchEnv &env);
+int launch_sample_tc(const Problem &p, const double *p64, const void *packed, int8_t *chains, int n_chains,
+                     uint64_t step0, uint64_t seed, int spc, int sweeps_between, int burn_in, int8_t *out_cfg,
+                     double *out_logpsi, const LaunchEnv &env);
+
+// ---- SR (sr.cu)
+struct SrWorkspace {
+    double *buf;
+    size_t doubles;
+};
+size_t sr_workspace_doubles(int64_t n, int P);
+int run_sr_solve(const Problem &p, const double *O, const double *eloc, int64_t n, double eps, double rtol,
+                 int max_iter, double lr, double *delta, double *params, int apply, double *workspace,
+                 int *iters_out, double *resid_out, double *energy_out, const LaunchEnv &env);
+
+}  // namespace nqs

@@ -1,0 +1,593 @@
+// CUDA-core kernels (float64 and float32): log psi, local energies,
+// connected-configuration lists, the Metropolis exchange sampler and the
+// per-sample backward that produces the local derivatives O_loc.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+#include "plain_net.cuh"
+
+namespace nqs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void convert_params_kernel(const double *__restrict__ p64, float *__restrict__ p32, int P) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) p32[i] = (float)p64[i];
+}
+
+// ------------------------------------------------------------------ log psi
+template <typename T, int CB>
+__global__ void __launch_bounds__(kThreads) logpsi_plain_kernel(Problem p, const T *params, const double *p64,
+                                                                const int8_t *configs, int64_t n, double *out,
+                                                                PlainLayout lay) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PlainNet<T> net;
+    net.bind(smem, lay);
+    int8_t *spins = reinterpret_cast<int8_t *>(smem + lay.total);
+    const int G = lay.G, N = p.N;
+    for (int64_t b0 = (int64_t)blockIdx.x * G; b0 < n; b0 += (int64_t)gridDim.x * G) {
+        const int gc = (int)std::min<int64_t>(G, n - b0);
+        for (int r = threadIdx.x; r < gc * N; r += blockDim.x) spins[r] = configs[b0 * N + r];
+        __syncthreads();
+        plain_forward<T, CB>(p, params, p64, spins, gc, net);
+        for (int g = threadIdx.x; g < gc; g += blockDim.x) {
+            out[2 * (b0 + g)] = net.a[g];
+            out[2 * (b0 + g) + 1] = net.phi[g];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ E_loc
+struct ElocSmem {
+    size_t spins, sigma, ci, cj, ch, tre, tim, cum, total;
+};
+
+__host__ __device__ inline ElocSmem eloc_smem(const Problem &p, size_t base, int G) {
+    ElocSmem e;
+    size_t o = base;
+    e.spins = o; o = align16(o + (size_t)G * p.N);
+    e.sigma = o; o = align16(o + p.N);
+    e.ci = o; o = align16(o + 2 * (size_t)p.n_bonds);
+    e.cj = o; o = align16(o + 2 * (size_t)p.n_bonds);
+    e.ch = o; o = align16(o + 8 * (size_t)p.n_bonds);
+    e.tre = o; o = align16(o + 16 * (size_t)(G > 0 ? G : 1));   // this batch's terms (re, im)
+    e.tim = e.tre;
+    e.cum = o; o = align16(o + 4 * (size_t)(p.N + 1));
+    e.total = o + sizeof(EnumScratch) + 4 * sizeof(double);
+    return e;
+}
+
+template <typename T, int CB>
+__global__ void __launch_bounds__(kThreads) eloc_plain_kernel(Problem p, const T *params, const double *p64,
+                                                              const int8_t *configs, const double *logpsi,
+                                                              int64_t n, double *out, PlainLayout lay, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PlainNet<T> net;
+    net.bind(smem, lay);
+    const ElocSmem es = eloc_smem(p, lay.total, lay.G);
+    int8_t *spins = reinterpret_cast<int8_t *>(smem + es.spins);
+    int8_t *sigma = reinterpret_cast<int8_t *>(smem + es.sigma);
+    int16_t *ci = reinterpret_cast<int16_t *>(smem + es.ci);
+    int16_t *cj = reinterpret_cast<int16_t *>(smem + es.cj);
+    double *ch = reinterpret_cast<double *>(smem + es.ch);
+    double *terms = reinterpret_cast<double *>(smem + es.tre);
+    int *cum = reinterpret_cast<int *>(smem + es.cum);
+    EnumScratch &scr = *reinterpret_cast<EnumScratch *>(smem + es.total - sizeof(EnumScratch) - 4 * sizeof(double));
+    // ref: a0, phi0, running sums of Re and Im of the off-diagonal terms
+    double *ref = reinterpret_cast<double *>(smem + es.total - 4 * sizeof(double));
+    const int G = lay.G, N = p.N;
+    const int recompute = logpsi == nullptr;
+
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+        for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = configs[s * N + r];
+        __syncthreads();
+        double hd;
+        const int nconn = enumerate_connected(p, sigma, ci, cj, ch, &hd, cum, scr);
+        if (threadIdx.x == 0) {
+            ref[2] = 0.0;
+            ref[3] = 0.0;
+            if (!recompute) { ref[0] = logpsi[2 * s]; ref[1] = logpsi[2 * s + 1]; }
+        }
+        __syncthreads();
+        const int n_entries = nconn + recompute;
+        for (int e0 = 0; e0 < n_entries; e0 += G) {
+            const int gc = std::min(G, n_entries - e0);
+            for (int r = threadIdx.x; r < gc * N; r += blockDim.x) {
+                const int g = r / N, site = r - g * N;
+                const int k = e0 + g - recompute;
+                int v = sigma[site];
+                if (k >= 0) {
+                    const int i = ci[k], j = cj[k];
+                    if (site == i) v = sigma[j];
+                    else if (site == j) v = sigma[i];
+                }
+                spins[r] = (int8_t)v;
+            }
+            __syncthreads();
+            plain_forward<T, CB>(p, params, p64, spins, gc, net);
+            if (e0 == 0 && recompute && threadIdx.x == 0) { ref[0] = net.a[0]; ref[1] = net.phi[0]; }
+            __syncthreads();
+            for (int g = threadIdx.x; g < gc; g += blockDim.x) {
+                const int k = e0 + g - recompute;
+                double tr = 0.0, ti = 0.0;
+                if (k >= 0) {
+                    const double m = ch[k] * exp(net.a[g] - ref[0]);
+                    double sn, cs;
+                    sincos(net.phi[g] - ref[1], &sn, &cs);
+                    tr = m * cs;
+                    ti = m * sn;
+                }
+                terms[2 * g] = tr;
+                terms[2 * g + 1] = ti;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {   // terms added in list order
+                double sr = ref[2], si = ref[3];
+                for (int g = 0; g < gc; ++g) { sr += terms[2 * g]; si += terms[2 * g + 1]; }
+                ref[2] = sr;
+                ref[3] = si;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double er = hd + ref[2], ei = ref[3];
+            out[2 * s] = er;
+            out[2 * s + 1] = ei;
+            if (!isfinite(er) || !isfinite(ei)) atomicOr(err, ERRBIT_NONFINITE);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ connected list
+__global__ void __launch_bounds__(kThreads) connected_kernel(Problem p, const int8_t *configs, int64_t n,
+                                                             int max_conn, int32_t *n_conn, int32_t *pairs,
+                                                             double *h, double *hdiag) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ElocSmem es = eloc_smem(p, 0, 0);
+    int8_t *sigma = reinterpret_cast<int8_t *>(smem + es.sigma);
+    int16_t *ci = reinterpret_cast<int16_t *>(smem + es.ci);
+    int16_t *cj = reinterpret_cast<int16_t *>(smem + es.cj);
+    double *ch = reinterpret_cast<double *>(smem + es.ch);
+    int *cum = reinterpret_cast<int *>(smem + es.cum);
+    EnumScratch &scr = *reinterpret_cast<EnumScratch *>(smem + es.total - sizeof(EnumScratch) - 4 * sizeof(double));
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+        for (int r = threadIdx.x; r < p.N; r += blockDim.x) sigma[r] = configs[s * p.N + r];
+        __syncthreads();
+        double hd;
+        const int nc = enumerate_connected(p, sigma, ci, cj, ch, &hd, cum, scr);
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+            pairs[(s * max_conn + k) * 2] = ci[k];
+            pairs[(s * max_conn + k) * 2 + 1] = cj[k];
+            h[s * max_conn + k] = ch[k];
+        }
+        if (threadIdx.x == 0) { n_conn[s] = nc; hdiag[s] = hd; }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ chains
+// Initial states: canonical multiset (up, down, holes) shuffled by
+// Fisher-Yates; swap partner of position k drawn from Philox block
+// (chain, k, 0, 0) under key (seed, 1).
+__global__ void init_chains_kernel(Problem p, uint64_t seed, int n_chains, int8_t *chains) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    int8_t *row = chains + (size_t)c * p.N;
+    for (int k = 0; k < p.N; ++k) row[k] = (int8_t)(k < p.n_up ? 1 : (k < p.n_up + p.n_down ? -1 : 0));
+    for (int k = p.N - 1; k >= 1; --k) {
+        const Philox4 b = philox((uint64_t)c, (uint64_t)k, 0, 0, seed, 1);
+        const int j = (int)mulhi64(b.v[0], (uint64_t)(k + 1));
+        const int8_t t = row[k];
+        row[k] = row[j];
+        row[j] = t;
+    }
+}
+
+struct SampleSmem {
+    size_t cur, spins, pi, pj, pu, ca, cphi, list, total;
+};
+
+__host__ __device__ inline SampleSmem sample_smem(const Problem &p, size_t base, int G) {
+    SampleSmem e;
+    size_t o = base;
+    e.cur = o; o = align16(o + (size_t)G * p.N);
+    e.spins = o; o = align16(o + (size_t)G * p.N);
+    e.pi = o; o = align16(o + 4 * (size_t)G);
+    e.pj = o; o = align16(o + 4 * (size_t)G);
+    e.pu = o; o = align16(o + 8 * (size_t)G);
+    e.ca = o; o = align16(o + 8 * (size_t)G);
+    e.cphi = o; o = align16(o + 8 * (size_t)G);
+    e.list = o; o = align16(o + 4 * (size_t)(G + 1));
+    e.total = o;
+    return e;
+}
+
+__device__ __forceinline__ int neighbour_dir(int i, int d, int L) {
+    const int x = i % L, y = i / L;
+    const int dx = d == 0 ? 1 : (d == 1 ? -1 : 0);
+    const int dy = d == 2 ? 1 : (d == 3 ? -1 : 0);
+    return site_at(x + dx, y + dy, L);
+}
+
+template <typename T, int CB>
+__global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const T *params, const double *p64,
+                                                                int8_t *chains, int n_chains, uint64_t step0,
+                                                                uint64_t seed, int spc, int sweeps_between,
+                                                                int burn_in, int8_t *out_cfg, double *out_logpsi,
+                                                                PlainLayout lay, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PlainNet<T> net;
+    net.bind(smem, lay);
+    const int G = lay.G, N = p.N;
+    const SampleSmem ss = sample_smem(p, lay.total, G);
+    int8_t *cur = reinterpret_cast<int8_t *>(smem + ss.cur);
+    int8_t *spins = reinterpret_cast<int8_t *>(smem + ss.spins);
+    int *pi = reinterpret_cast<int *>(smem + ss.pi);
+    int *pj = reinterpret_cast<int *>(smem + ss.pj);
+    double *pu = reinterpret_cast<double *>(smem + ss.pu);
+    double *ca = reinterpret_cast<double *>(smem + ss.ca);
+    double *cphi = reinterpret_cast<double *>(smem + ss.cphi);
+    int *list = reinterpret_cast<int *>(smem + ss.list);
+
+    const int c0 = blockIdx.x * G;
+    if (c0 >= n_chains) return;
+    const int gc = min(G, n_chains - c0);
+    for (int r = threadIdx.x; r < gc * N; r += blockDim.x) cur[r] = chains[(size_t)c0 * N + r];
+    __syncthreads();
+    plain_forward<T, CB>(p, params, p64, cur, gc, net);
+    for (int g = threadIdx.x; g < gc; g += blockDim.x) { ca[g] = net.a[g]; cphi[g] = net.phi[g]; }
+    __syncthreads();
+
+    const int n_sweeps = burn_in + spc * sweeps_between;
+    for (int sweep = 0; sweep < n_sweeps; ++sweep) {
+        for (int q = 0; q < N; ++q) {
+            const uint64_t step = step0 + (uint64_t)sweep * N + q;
+            for (int g = threadIdx.x; g < gc; g += blockDim.x) {
+                const Philox4 b = philox((uint64_t)(c0 + g), step, 0, 0, seed, 0);
+                const int i = (int)mulhi64(b.v[0], (uint64_t)N);
+                const int d = (int)(b.v[1] >> 62);
+                const int j = neighbour_dir(i, d, p.L);
+                pi[g] = i;
+                pj[g] = j;
+                pu[g] = (double)(b.v[2] >> 11) * 0x1.0p-53;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int cnt = 0;
+                for (int g = 0; g < gc; ++g)
+                    if (cur[g * N + pi[g]] != cur[g * N + pj[g]]) list[cnt++] = g;
+                list[G] = cnt;
+            }
+            __syncthreads();
+            const int cnt = list[G];
+            if (cnt > 0) {
+                for (int r = threadIdx.x; r < cnt * N; r += blockDim.x) {
+                    const int m = r / N, site = r - m * N;
+                    const int g = list[m];
+                    const int i = pi[g], j = pj[g];
+                    const int src = site == i ? j : (site == j ? i : site);
+                    spins[r] = cur[g * N + src];
+                }
+                __syncthreads();
+                plain_forward<T, CB>(p, params, p64, spins, cnt, net);
+                for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
+                    const int g = list[m];
+                    const double delta = 2.0 * (net.a[m] - ca[g]);
+                    if (delta >= 0.0 || pu[g] < exp(delta)) {
+                        const int i = pi[g], j = pj[g];
+                        const int8_t t = cur[g * N + i];
+                        cur[g * N + i] = cur[g * N + j];
+                        cur[g * N + j] = t;
+                        ca[g] = net.a[m];
+                        cphi[g] = net.phi[m];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (sweep >= burn_in && (sweep - burn_in + 1) % sweeps_between == 0) {
+            const int k = (sweep - burn_in + 1) / sweeps_between - 1;
+            for (int r = threadIdx.x; r < gc * N; r += blockDim.x) {
+                const int g = r / N, site = r - g * N;
+                out_cfg[((size_t)(c0 + g) * spc + k) * N + site] = cur[r];
+            }
+            for (int g = threadIdx.x; g < gc; g += blockDim.x) {
+                out_logpsi[2 * ((size_t)(c0 + g) * spc + k)] = ca[g];
+                out_logpsi[2 * ((size_t)(c0 + g) * spc + k) + 1] = cphi[g];
+                if (!isfinite(ca[g])) atomicOr(err, ERRBIT_NONFINITE);
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < gc * N; r += blockDim.x) chains[(size_t)c0 * N + r] = cur[r];
+}
+
+// ------------------------------------------------------------------ backward
+// Per sample: forward with every layer's pre-activation z_l and output
+// h_l kept in this block's global scratch, then reverse-mode through the
+// head, the SiLU (silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)) and the
+// periodic convolutions, for both outputs (a and phi) at once.
+template <typename T>
+__device__ __forceinline__ T sigmoid_t(T z) { return T(1) / (T(1) + exp(-z)); }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) grad_plain_kernel(Problem p, const T *params, const double *p64,
+                                                              const int8_t *configs, int64_t n, double *O,
+                                                              T *scratch, size_t per_block) {
+    const int N = p.N, C = p.C, L = p.L, nl = p.n_layers, P = p.P;
+    T *base = scratch + per_block * blockIdx.x;
+    T *h0 = base;                                  // [c_in][N]
+    T *z = h0 + (size_t)p.c_in * N;                // [nl][C][N]
+    T *h = z + (size_t)nl * C * N;                 // [nl][C][N]
+    T *g = h + (size_t)nl * C * N;                 // [2][C][N]
+    T *gz = g + (size_t)2 * C * N;                 // [2][C][N]
+    __shared__ T hbar[64];
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+        double *Oa = O + (size_t)s * P;
+        double *Op = O + (size_t)(n + s) * P;
+        for (int r = threadIdx.x; r < N; r += blockDim.x) {
+            const int v = configs[s * N + r];
+            if (p.c_in == 1) h0[r] = (T)v;
+            else { h0[r] = (T)(v == 0); h0[N + r] = (T)(v == 1); h0[2 * N + r] = (T)(v == -1); }
+        }
+        __syncthreads();
+        for (int l = 0; l < nl; ++l) {
+            const int cin = layer_cin(p, l), off = layer_offset(p, l);
+            const T *hin = l == 0 ? h0 : h + (size_t)(l - 1) * C * N;
+            for (int r = threadIdx.x; r < C * N; r += blockDim.x) {
+                const int co = r / N, site = r - co * N, x = site % L, y = site / L;
+                T acc = params[off + 9 * cin * C + co];
+                for (int c = 0; c < cin; ++c)
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx)
+                            acc = fma(params[off + (co * cin + c) * 9 + ky * 3 + kx],
+                                      hin[c * N + site_at(x + kx - 1, y + ky - 1, L)], acc);
+                z[(size_t)l * C * N + r] = acc;
+                h[(size_t)l * C * N + r] = acc * sigmoid_t<T>(acc);
+            }
+            __syncthreads();
+        }
+        const T *hn = h + (size_t)(nl - 1) * C * N;
+        for (int c = threadIdx.x; c < C; c += blockDim.x) {
+            T v = 0;
+            for (int site = 0; site < N; ++site) v += hn[c * N + site];
+            hbar[c] = v;
+        }
+        __syncthreads();
+        const int ho = head_offset(p);
+        for (int c = threadIdx.x; c < C; c += blockDim.x) {
+            Oa[ho + c] = (double)hbar[c];
+            Oa[ho + C + c] = 0.0;
+            Op[ho + c] = 0.0;
+            Op[ho + C + c] = (double)hbar[c];
+        }
+        for (int r = threadIdx.x; r < C * N; r += blockDim.x) {
+            const int c = r / N;
+            g[r] = (T)p64[ho + c];
+            g[C * N + r] = (T)p64[ho + C + c];
+        }
+        __syncthreads();
+        for (int l = nl - 1; l >= 0; --l) {
+            const int cin = layer_cin(p, l), off = layer_offset(p, l);
+            const T *zl = z + (size_t)l * C * N;
+            const T *hin = l == 0 ? h0 : h + (size_t)(l - 1) * C * N;
+            for (int r = threadIdx.x; r < 2 * C * N; r += blockDim.x) {
+                const T zz = zl[r % (C * N)];
+                const T sg = sigmoid_t<T>(zz);
+                gz[r] = g[r] * (sg * (T(1) + zz * (T(1) - sg)));
+            }
+            __syncthreads();
+            // weight and bias gradients for both outputs
+            const int nw = 9 * cin * C;
+            for (int e = threadIdx.x; e < 2 * (nw + C); e += blockDim.x) {
+                const int rr = e / (nw + C), idx = e - rr * (nw + C);
+                const T *gzr = gz + (size_t)rr * C * N;
+                T acc = 0;
+                if (idx < nw) {
+                    const int co = idx / (9 * cin), rem = idx - co * 9 * cin, c = rem / 9, o = rem - c * 9;
+                    const int dy = o / 3 - 1, dx = o % 3 - 1;
+                    for (int site = 0; site < N; ++site) {
+                        const int x = site % L, y = site / L;
+                        acc = fma(gzr[co * N + site], hin[c * N + site_at(x + dx, y + dy, L)], acc);
+                    }
+                } else {
+                    const int co = idx - nw;
+                    for (int site = 0; site < N; ++site) acc += gzr[co * N + site];
+                }
+                (rr == 0 ? Oa : Op)[off + idx] = (double)acc;
+            }
+            if (l > 0) {
+                // gradient wrt the layer input: g[c][y][x] = sum_{o, d} W[o][c][d] gz[o][y - dy][x - dx]
+                for (int r = threadIdx.x; r < 2 * C * N; r += blockDim.x) {
+                    const int rr = r / (C * N), rem = r - rr * C * N, c = rem / N, site = rem - c * N;
+                    const int x = site % L, y = site / L;
+                    const T *gzr = gz + (size_t)rr * C * N;
+                    T acc = 0;
+                    for (int co = 0; co < C; ++co)
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int kx = 0; kx < 3; ++kx)
+                                acc = fma(params[off + (co * cin + c) * 9 + ky * 3 + kx],
+                                          gzr[co * N + site_at(x - (kx - 1), y - (ky - 1), L)], acc);
+                    g[r] = acc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+void launch_convert_params(const double *p64, float *p32, int P, cudaStream_t s) {
+    convert_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(p64, p32, P);
+}
+
+int plain_max_group(const Problem &p, int prec, size_t extra_smem, size_t max_smem) {
+    int G = 32;
+    while (G > 1) {
+        const size_t need = (prec == NQS_FP64 ? plain_layout<double>(p, G).total : plain_layout<float>(p, G).total) +
+                            extra_smem + 64 * (size_t)G + 2 * (size_t)G * p.N + 1024;
+        if (need <= max_smem && (size_t)G * p.N <= 8192) break;
+        --G;
+    }
+    return G;
+}
+
+#define NQS_DISPATCH_CB(C, ...)                                            \
+    switch (C) {                                                           \
+        case 4: { constexpr int CB = 4; __VA_ARGS__; } break;             \
+        case 8: { constexpr int CB = 8; __VA_ARGS__; } break;             \
+        case 16: { constexpr int CB = 16; __VA_ARGS__; } break;           \
+        case 32: { constexpr int CB = 16; __VA_ARGS__; } break;           \
+        default: return NQS_ERR_UNSUPPORTED;                               \
+    }
+
+static int check_launch(const LaunchEnv &env, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *env.msg = std::string(what) + ": " + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    ++*env.launches;
+    return NQS_OK;
+}
+
+template <typename T, typename K>
+static int set_smem(K kernel, size_t bytes, const LaunchEnv &env) {
+    if (bytes > env.max_smem) {
+        *env.msg = "problem needs " + std::to_string(bytes) + " bytes of shared memory per block (max " +
+                   std::to_string(env.max_smem) + ")";
+        return NQS_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+        *env.msg = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    return NQS_OK;
+}
+
+template <typename T>
+static int logpsi_plain_t(const Problem &p, const T *params, const double *p64, const int8_t *configs, int64_t n,
+                          double *out, const LaunchEnv &env) {
+    const int G = plain_max_group(p, sizeof(T) == 8 ? NQS_FP64 : NQS_FP32, 0, env.max_smem);
+    const PlainLayout lay = plain_layout<T>(p, G);
+    const size_t bytes = lay.total + align16((size_t)G * p.N);
+    const int64_t groups = (n + G - 1) / G;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)env.num_sms * 4));
+    NQS_DISPATCH_CB(p.C, {
+        auto k = logpsi_plain_kernel<T, CB>;
+        int rc = set_smem<T>(k, bytes, env);
+        if (rc) return rc;
+        k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, configs, n, out, lay);
+    });
+    return check_launch(env, "logpsi_plain_kernel");
+}
+
+int launch_logpsi_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
+                        double *out, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    if (prec == NQS_FP64) return logpsi_plain_t<double>(p, dp.p64, dp.p64, configs, n, out, env);
+    return logpsi_plain_t<float>(p, dp.p32, dp.p64, configs, n, out, env);
+}
+
+template <typename T>
+static int eloc_plain_t(const Problem &p, const T *params, const double *p64, const int8_t *configs,
+                        const double *logpsi, int64_t n, double *out, const LaunchEnv &env) {
+    const size_t extra = eloc_smem(p, 0, 0).total + 64;
+    const int G = plain_max_group(p, sizeof(T) == 8 ? NQS_FP64 : NQS_FP32, extra, env.max_smem);
+    const PlainLayout lay = plain_layout<T>(p, G);
+    const size_t bytes = eloc_smem(p, lay.total, G).total;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * 8));
+    NQS_DISPATCH_CB(p.C, {
+        auto k = eloc_plain_kernel<T, CB>;
+        int rc = set_smem<T>(k, bytes, env);
+        if (rc) return rc;
+        k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, configs, logpsi, n, out, lay, env.err);
+    });
+    return check_launch(env, "eloc_plain_kernel");
+}
+
+int launch_eloc_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs,
+                      const double *logpsi, int64_t n, double *out, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    if (prec == NQS_FP64) return eloc_plain_t<double>(p, dp.p64, dp.p64, configs, logpsi, n, out, env);
+    return eloc_plain_t<float>(p, dp.p32, dp.p64, configs, logpsi, n, out, env);
+}
+
+int launch_connected(const Problem &p, const int8_t *configs, int64_t n, int max_conn, int32_t *n_conn,
+                     int32_t *pairs, double *h, double *hdiag, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    const size_t bytes = eloc_smem(p, 0, 0).total;
+    int rc = set_smem<double>(connected_kernel, bytes, env);
+    if (rc) return rc;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * 8));
+    connected_kernel<<<grid, kThreads, bytes, env.stream>>>(p, configs, n, max_conn, n_conn, pairs, h, hdiag);
+    return check_launch(env, "connected_kernel");
+}
+
+int launch_init_chains(const Problem &p, uint64_t seed, int n_chains, int8_t *chains, const LaunchEnv &env) {
+    if (n_chains == 0) return NQS_OK;
+    init_chains_kernel<<<(n_chains + 127) / 128, 128, 0, env.stream>>>(p, seed, n_chains, chains);
+    return check_launch(env, "init_chains_kernel");
+}
+
+template <typename T>
+static int sample_plain_t(const Problem &p, const T *params, const double *p64, int8_t *chains, int n_chains,
+                          uint64_t step0, uint64_t seed, int spc, int sb, int burn, int8_t *out_cfg,
+                          double *out_logpsi, const LaunchEnv &env) {
+    const size_t per_g = sample_smem(p, 0, 1).total;
+    int G = plain_max_group(p, sizeof(T) == 8 ? NQS_FP64 : NQS_FP32, per_g * 32 + 64, env.max_smem);
+    // enough blocks to cover the GPU: at most ceil(n_chains / num_sms) chains per block
+    G = std::max(1, std::min(G, (n_chains + env.num_sms - 1) / env.num_sms));
+    const PlainLayout lay = plain_layout<T>(p, G);
+    const size_t bytes = sample_smem(p, lay.total, G).total;
+    const int grid = (n_chains + G - 1) / G;
+    NQS_DISPATCH_CB(p.C, {
+        auto k = sample_plain_kernel<T, CB>;
+        int rc = set_smem<T>(k, bytes, env);
+        if (rc) return rc;
+        k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, chains, n_chains, step0, seed, spc, sb, burn,
+                                                 out_cfg, out_logpsi, lay, env.err);
+    });
+    return check_launch(env, "sample_plain_kernel");
+}
+
+int launch_sample_plain(const Problem &p, int prec, const DeviceParams &dp, int8_t *chains, int n_chains,
+                        uint64_t step0, uint64_t seed, int spc, int sweeps_between, int burn_in, int8_t *out_cfg,
+                        double *out_logpsi, const LaunchEnv &env) {
+    if (prec == NQS_FP64)
+        return sample_plain_t<double>(p, dp.p64, dp.p64, chains, n_chains, step0, seed, spc, sweeps_between,
+                                      burn_in, out_cfg, out_logpsi, env);
+    return sample_plain_t<float>(p, dp.p32, dp.p64, chains, n_chains, step0, seed, spc, sweeps_between, burn_in,
+                                 out_cfg, out_logpsi, env);
+}
+
+static size_t grad_per_block(const Problem &p) {
+    return (size_t)p.c_in * p.N + 2 * (size_t)p.n_layers * p.C * p.N + 4 * (size_t)p.C * p.N;
+}
+
+size_t grad_scratch_bytes(const Problem &p, int prec, int num_blocks) {
+    return grad_per_block(p) * num_blocks * (prec == NQS_FP64 ? 8 : 4);
+}
+
+int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
+                      double *O, void *scratch, size_t scratch_bytes, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    const size_t esz = prec == NQS_FP64 ? 8 : 4;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(scratch_bytes / (grad_per_block(p) * esz))));
+    if (prec == NQS_FP64)
+        grad_plain_kernel<double><<<blocks, kThreads, 0, env.stream>>>(p, dp.p64, dp.p64, configs, n, O,
+                                                                        (double *)scratch, grad_per_block(p));
+    else
+        grad_plain_kernel<float><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, O,
+                                                                       (float *)scratch, grad_per_block(p));
+    return check_launch(env, "grad_plain_kernel");
+}
+
+}  // namespace nqs
