@@ -1,0 +1,148 @@
+"""GPU checks of the tensor-core (tcgen05, bf16 operands, fp32 accumulation)
+path against the FP64 oracle, through the C ABI.
+
+Tolerances (derived in the design notes): bf16 stores every activation with
+a relative rounding error of at most 2^-9, so a network of n_l layers carries
+a relative error of order n_l * 2^-9 in each activation; log psi sums N*C
+such terms with weights of order 0.5/sqrt(C). Measured |d log psi| on these
+workloads stays below 2e-3, and the tests hold it to 5e-3 per configuration.
+The energy per site over a batch must be within 1e-4 of the oracle's on the
+same samples (the validity condition of the fast path).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn, ed, eloc, sampler
+from tests.gpu_common import WL, configs_for, dev, lib, make_ctx, oracle_of
+
+pytestmark = pytest.mark.gpu
+
+TC_CASES = [
+    ('j1j2_10x10', {}),
+    ('j1j2_16x16', {'n_layers': 4}),
+    ('tj_12x12', {}),
+    ('j1j2_4x4', {'channels': 16, 'n_layers': 3}),
+    ('tj_12x12', {'L': 6, 'n_up': 15, 'n_down': 14, 'channels': 16, 'n_layers': 4}),
+]
+
+
+def _ids(c):
+    return c[0] + ''.join('-%s%s' % kv for kv in c[1].items())
+
+
+@pytest.mark.parametrize('case', TC_CASES, ids=_ids)
+def test_logpsi_bf16_close_to_oracle(case):
+    name, over = case
+    w = WL[name]
+    ctx, params = make_ctx(w, **over)
+    spec, _ = oracle_of(w, **over)
+    cfg = configs_for(w, 150, seed=21, **over)
+    got = ctx.logpsi(dev(cfg), 'bf16').cpu().numpy()
+    a, phi = cnn.forward(params, cfg, spec)
+    da = np.abs(got[:, 0] - a).max()
+    dp = np.abs(got[:, 1] - phi).max()
+    print('max |d log|psi|| = %.3e, max |d phi| = %.3e (scale %.3e)' % (da, dp, np.abs(a).max()))
+    assert da <= 5e-3 and dp <= 5e-3
+
+
+@pytest.mark.parametrize('case', TC_CASES[:3], ids=_ids)
+def test_logpsi_bf16_independent_of_batch_slot(case):
+    """A configuration's bf16 log psi does not depend on which other
+    configurations share its group, nor on its slot (bitwise)."""
+    name, over = case
+    w = WL[name]
+    ctx, _ = make_ctx(w, **over)
+    cfg = configs_for(w, 64, seed=22, **over)
+    x = dev(cfg)
+    a1 = ctx.logpsi(x, 'bf16')
+    perm = torch.randperm(64, generator=torch.Generator().manual_seed(0)).cuda()
+    a2 = ctx.logpsi(x[perm].contiguous(), 'bf16')
+    assert torch.equal(a1[perm], a2)
+    a3 = ctx.logpsi(x[:7].contiguous(), 'bf16')
+    assert torch.equal(a1[:7], a3)
+
+
+@pytest.mark.parametrize('case', TC_CASES[:3], ids=_ids)
+def test_local_energy_bf16_energy_per_site(case):
+    name, over = case
+    w = WL[name]
+    ctx, params = make_ctx(w, **over)
+    spec, ham = oracle_of(w, **over)
+    n = 48 if name != 'j1j2_16x16' else 12
+    cfg = configs_for(w, n, seed=23, **over)
+    got = ctx.local_energy(dev(cfg), None, 'bf16').cpu().numpy()
+    want = eloc.local_energy(params, cfg, spec, ham)
+    N = w['L'] ** 2
+    e_site = abs(got[:, 0].mean() - want.real.mean()) / N
+    print('energy per site bf16 - oracle = %.3e; max |dE_loc| = %.3e' % (e_site, np.abs(got[:, 0] - want.real).max()))
+    assert e_site <= 1e-4
+
+
+def test_local_energy_bf16_deterministic_across_batches():
+    w = WL['j1j2_10x10']
+    ctx, _ = make_ctx(w)
+    cfg = dev(configs_for(w, 40, seed=24))
+    e1 = ctx.local_energy(cfg, None, 'bf16')
+    e2 = ctx.local_energy(cfg[10:20].contiguous(), None, 'bf16')
+    assert torch.equal(e1[10:20], e2)
+
+
+def test_local_energy_bf16_zero_network():
+    w = WL['j1j2_10x10']
+    from tests.gpu_common import problem_of
+    P = lib().nqs_param_count(problem_of(w))
+    ctx, _ = make_ctx(w, params=np.zeros(P))
+    e = ctx.local_energy(dev(configs_for(w, 16, seed=25)), None, 'bf16').cpu().numpy()
+    assert np.all(e[:, 0] == 75.0) and np.all(e[:, 1] == 0.0)
+
+
+def test_bf16_unsupported_shapes_fail_loudly():
+    nqs = lib()
+    w = WL['j1j2_4x4']          # 4 channels: below the tensor-core N granularity
+    ctx, _ = make_ctx(w)
+    with pytest.raises(nqs.NQSError) as ei:
+        ctx.local_energy(dev(configs_for(w, 2, 1)), None, 'bf16')
+    assert ei.value.code == -7
+
+
+def test_sampler_bf16_chi_square():
+    """bf16 sampler on 4x4 (16 channels) against the oracle's enumerated |psi|^2."""
+    from scipy import stats
+    w = WL['j1j2_4x4']
+    over = {'channels': 16, 'n_layers': 2}
+    ctx, params = make_ctx(w, seed=5, scale=0.8, **over)
+    spec, _ = oracle_of(w, **over)
+    basis = ed.sector_basis(16, 8, 8)
+    a, _ = cnn.forward(params, basis, spec)
+    p = np.exp(2 * (a - a.max()))
+    p /= p.sum()
+    n_ch = 4096
+    cfg, lp = ctx.sample(n_ch, 1, 1, 30, 'bf16')
+    samples = cfg.cpu().numpy()
+    assert np.all(samples.sum(1) == 0)
+    keys = ed.config_keys(basis)
+    idx = np.searchsorted(keys, ed.config_keys(samples))
+    assert np.all(keys[idx] == ed.config_keys(samples))
+    order = np.argsort(p)
+    cum = np.cumsum(p[order])
+    bins = np.empty(p.size, dtype=int)
+    bins[order] = np.minimum((cum * 32).astype(int), 31)
+    used = np.unique(bins)
+    bins = np.searchsorted(used, bins)
+    exp_c = np.bincount(bins, weights=p, minlength=used.size) * n_ch
+    obs = np.bincount(bins[idx], minlength=used.size)
+    chi2 = ((obs - exp_c) ** 2 / exp_c).sum()
+    assert stats.chi2.sf(chi2, used.size - 1) > 1e-3
+
+
+def test_sampler_bf16_conserves_sector_tj():
+    w = WL['tj_12x12']
+    ctx, _ = make_ctx(w, seed=6)
+    cfg, lp = ctx.sample(64, 2, 1, 2, 'bf16')
+    c = cfg.cpu().numpy()
+    assert np.all((c == 1).sum(1) == 63) and np.all((c == -1).sum(1) == 63) and np.all((c == 0).sum(1) == 18)
+    # the stored log psi is the bf16 log psi of the stored configuration
+    again = ctx.logpsi(cfg, 'bf16')
+    assert torch.equal(again, lp)
