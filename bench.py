@@ -42,7 +42,39 @@ def parse():
     ap.add_argument('--workload', default='j1j2_10x10')
     ap.add_argument('--compare-steps', type=int, default=2, help='steps of the plain FP32 path')
     ap.add_argument('--oracle-samples', type=int, default=256, help='bounded sample for the CPU oracle')
+    ap.add_argument('--profile-eloc', type=int, default=0, metavar='S',
+                    help='profiling mode: only run --steps E_loc passes over S uniform random samples')
     return ap.parse_args()
+
+
+def profile_eloc(args):
+    """Small, self-contained E_loc run for profilers (no sampler, no SR)."""
+    import numpy as np
+    import torch
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300 import nqs
+    nbuild.build()
+    w = nqs_synth.WORKLOADS[args.workload]
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    prob = (nqs.make_problem('j1j2', w['L'], J1=w['J1'], J2=w['J2'], n_layers=w['n_layers'], channels=w['channels'])
+            if w['model'] == 'j1j2' else
+            nqs.make_problem('tj', w['L'], t=w['t'], J=w['J'], n_up=w['n_up'], n_down=w['n_down'],
+                             n_layers=w['n_layers'], channels=w['channels']))
+    ctx = nqs.Context(prob, torch.tensor(params, dtype=torch.float64, device='cuda'), seed=1)
+    cfg = torch.from_numpy(nqs_synth.random_configs(w['L'] ** 2, w['n_up'], w['n_down'], args.profile_eloc, 3)).cuda()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.local_energy(cfg, None, args.precision)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.sync()
+    print(json.dumps({'mode': 'profile-eloc', 'workload': args.workload, 'samples': args.profile_eloc,
+                      'precision': args.precision, 'ms': times, 'samples_per_s': args.profile_eloc / (min(times) / 1e3)}))
 
 
 def dense_forward_flops(w):
@@ -191,6 +223,9 @@ def main():
     args = parse()
     if args.impl == 'reference':
         run_reference(args)
+        return
+    if args.profile_eloc:
+        profile_eloc(args)
         return
     # the oracle's process pool is started before the first GPU call
     rank = int(os.environ.get('RANK', '0'))

@@ -12,9 +12,12 @@
 // one tcgen05.mma whose A descriptor starts at a shifted address (an
 // implicit GEMM with no im2col copy): M = 128 rows, N = C, K = 16.
 // Halo rows are refreshed by the epilogue, which writes every interior
-// output also to its periodic images. Weights of the next layer stream in
-// by bulk copy (TMA) while the current layer computes. Layer 0 (one spin
-// channel or three one-hot channels) runs on CUDA cores in fp32.
+// output also to its periodic images (a per-row destination table built
+// once per kernel). Weights of the next layer stream in by bulk copy (TMA)
+// while the current layer computes. Each 128-row tile commits to its own
+// mbarrier, so the epilogue of tile t overlaps the MMAs of later tiles.
+// Layer 0 (one spin channel or three one-hot channels) runs on CUDA cores
+// in fp32 from a padded copy of the spins.
 #include <algorithm>
 #include <cmath>
 
@@ -28,6 +31,9 @@ namespace nqs {
 namespace {
 
 constexpr int kTcThreads = 256;   // 8 warps: warp w reads TMEM lanes 32 (w % 4) ...; tiles split by w / 4
+constexpr int kMaxTiles = 16;
+constexpr int kIssuers = 4;       // threads issuing tcgen05.mma (lane 0 of warps 0..3)
+constexpr uint32_t kNone = 0xFFFFu;
 
 struct TcPlan {
     int L, Lp, N, G, C, KC, c_in, n_layers, n_tc;
@@ -37,28 +43,27 @@ struct TcPlan {
     uint32_t f32_count;    // 9 c_in C + n_layers C + 2 C floats
     uint32_t f32_bytes;    // padded to 16
     // shared-memory offsets
-    uint32_t o_act0, o_act1, o_w0, o_w1, o_f32, o_spins, o_res, o_bar, o_extra, total;
+    uint32_t o_act0, o_act1, o_w0, o_w1, o_f32, o_rowtab, o_sitetab, o_spad, o_spins, o_res, o_bar, o_extra, total;
 };
 
 __host__ __device__ inline uint32_t al16(uint32_t v) { return (v + 15u) & ~15u; }
 
-// log psi results of a group: a[G], phi[G] (double), then scratch
-struct GroupResults {
-    double *a, *phi;
-};
-
 struct TcShared {
     unsigned char *base;
-    uint64_t *bar_mma, *bar_w;   // bar_w[2]
+    uint64_t *bar_w;             // [2] weight buffers
+    uint64_t *bar_tile;          // [kMaxTiles] per-tile MMA completion
     uint32_t *tmem_addr;
     int *abort_flag;
-    int8_t *spins;
+    int8_t *spins;               // [G][N] the group's configurations
+    int8_t *spad;                // [Lp * Lp * G] padded copy, row = pos * G + g
+    const uint2 *rowtab;         // [n_tiles * 128] destination rows of each output row
+    const uint2 *sitetab;        // [N] padded positions of each site (main + images)
     float *f32;                  // w0s [9][c_in][C], biases [n_layers][C], head [2][C]
-    GroupResults res;
+    double *a, *phi;             // [G] results
 };
 
 struct TcState {        // per-CTA pipeline state (all threads keep identical copies)
-    uint32_t mma_phase;
+    uint32_t layers;    // tensor-core layers executed so far (tile-barrier parity)
     uint32_t wseq;      // weight loads consumed so far
     uint32_t wissued;   // weight loads issued so far
 };
@@ -77,9 +82,18 @@ __device__ __forceinline__ void issue_weight_load(const TcPlan &pl, const TcShar
     ptx::bulk_g2s(dst, tc_layer_weights(pl, packed, l), pl.wbytes, &sh.bar_w[b]);
 }
 
+// Wait on an mbarrier phase; gives up when another thread raised the abort
+// flag or after the iteration limit.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, const int *abort_flag) {
+    for (long long it = 0; it < ptx::kWaitLimit; ++it) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && *(volatile const int *)abort_flag) return false;
+    }
+    return false;
+}
+
 // Padded positions holding interior site (x, y) and its periodic images.
-__device__ __forceinline__ int images(const TcPlan &pl, int x, int y, int (&pos)[4]) {
-    const int L = pl.L, Lp = pl.Lp;
+__device__ __forceinline__ int images(int L, int Lp, int x, int y, int (&pos)[4]) {
     const int ys[2] = {y + 1, y == 0 ? L + 1 : (y == L - 1 ? 0 : -1)};
     const int xs[2] = {x + 1, x == 0 ? L + 1 : (x == L - 1 ? 0 : -1)};
     int n = 0;
@@ -91,37 +105,45 @@ __device__ __forceinline__ int images(const TcPlan &pl, int x, int y, int (&pos)
     return n;
 }
 
+__device__ __forceinline__ uint2 pack4(const int (&v)[4], int n) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = i < n ? (uint32_t)v[i] : kNone;
+    return make_uint2(w[0] | (w[1] << 16), w[2] | (w[3] << 16));
+}
+
 template <int C>
-__device__ __forceinline__ void store_row_images(const TcPlan &pl, uint32_t act, int x, int y, int g,
-                                                 const uint32_t (&w)[C / 2]) {
-    int pos[4];
-    const int n = images(pl, x, y, pos);
-    for (int i = 0; i < n; ++i) {
-        const uint32_t row = (uint32_t)(pos[i] * pl.G + g);
+__device__ __forceinline__ void store_rows(const TcPlan &pl, uint32_t act, uint2 dst, const uint32_t (&w)[C / 2]) {
+    const uint32_t d[4] = {dst.x & 0xFFFFu, dst.x >> 16, dst.y & 0xFFFFu, dst.y >> 16};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (d[i] == kNone) break;
 #pragma unroll
         for (int kc = 0; kc < C / 8; ++kc)
-            ptx::st_shared_v4(act + kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+            ptx::st_shared_v4(act + kc * pl.plane + d[i] * 16u, w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
     }
 }
 
-// Layer 0 on CUDA cores: input channels from the spins, fp32 weights.
+// Layer 0 on CUDA cores: input channels from the padded spins, fp32 weights.
+// Each thread handles the same output rows as in the tensor-core epilogue.
 template <int C>
 __device__ void layer0(const TcPlan &pl, const TcShared &sh, uint32_t act_out) {
-    const int N = pl.N, L = pl.L, G = pl.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
     const float *w0 = sh.f32;                         // [9][c_in][C]
     const float *b0 = sh.f32 + 9 * pl.c_in * C;       // bias of layer 0
-    for (int r = threadIdx.x; r < N * G; r += blockDim.x) {
-        const int site = r / G, g = r - site * G;
-        const int x = site % L, y = site / L;
+    int offg[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) offg[o] = ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * pl.G;
+    for (int t = warp >> 2; t < pl.n_tiles; t += kTcThreads / 128) {
+        const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
+        const uint32_t main = dst.x & 0xFFFFu;
+        if (main == kNone) continue;
         float z[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) z[c] = b0[c];
-        const int8_t *sp = sh.spins + g * N;
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
-            const int yy = y + o / 3 - 1, xx = x + o % 3 - 1;
-            const int nb = ((yy + L) % L) * L + (xx + L) % L;
-            const int s = sp[nb];
+            const int s = sh.spad[(int)main + offg[o]];
             if (pl.c_in == 1) {
                 const float fs = (float)s;
                 const float *wr = w0 + o * C;
@@ -137,21 +159,32 @@ __device__ void layer0(const TcPlan &pl, const TcShared &sh, uint32_t act_out) {
         uint32_t w[C / 2];
 #pragma unroll
         for (int c = 0; c < C / 2; ++c) w[c] = ptx::pack_bf16(ptx::silu_fast(z[2 * c]), ptx::silu_fast(z[2 * c + 1]));
-        store_row_images<C>(pl, act_out, x, y, g, w);
+        store_rows<C>(pl, act_out, dst, w);
     }
 }
 
-// Evaluate the G configurations in sh.spins; results to sh.res (double).
-// Returns false if a wait timed out (the block must stop).
+// Evaluate the G configurations in sh.spins; results to sh.a / sh.phi
+// (double). Returns false if a wait timed out (the block must stop).
 template <int C>
 __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st,
                                  int *err) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
     const uint32_t act[2] = {ptx::smem_u32(sh.base + pl.o_act0), ptx::smem_u32(sh.base + pl.o_act1)};
     const uint32_t tmem = *sh.tmem_addr;
     const uint32_t idesc = ptx::idesc_bf16(128, C);
-    const int G = pl.G, Lp = pl.Lp, L = pl.L;
+    const int G = pl.G;
 
+    // padded spins: every site to its main position and periodic images
+    for (int r = threadIdx.x; r < G * pl.N; r += blockDim.x) {
+        const int g = r / pl.N, site = r - g * pl.N;
+        const uint2 pos = sh.sitetab[site];
+        const int8_t v = sh.spins[r];
+        const uint32_t d[4] = {pos.x & 0xFFFFu, pos.x >> 16, pos.y & 0xFFFFu, pos.y >> 16};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (d[i] != kNone) sh.spad[d[i] * G + g] = v;
+    }
+    __syncthreads();
     layer0<C>(pl, sh, act[0]);
     ptx::fence_async_smem();
     __syncthreads();
@@ -159,31 +192,36 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
     int cur = 0;
     for (int l = 1; l < pl.n_layers; ++l) {
         const bool last = (l == pl.n_layers - 1);
-        if (threadIdx.x == 0) {
+        const uint32_t parity = st.layers & 1u;
+        // four issuing threads (lane 0 of warps 0-3, one per SM sub-partition),
+        // issuer w owns tiles w, w + 4, ...; each tile commits to its own barrier
+        if (lane == 0 && warp < kIssuers) {
             const uint32_t q = st.wseq;
-            bool ok = ptx::mbar_wait(&sh.bar_w[q & 1], (q >> 1) & 1);
-            if (ok) {
+            if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
                 // prefetch the next load into the other buffer (its last reader, load q - 1, has completed)
-                issue_weight_load(pl, sh, packed, q + 1);
+                if (warp == 0) issue_weight_load(pl, sh, packed, q + 1);
                 ptx::tc_fence_after();
-                const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
-                const uint32_t a0 = act[cur];
-                for (int t = 0; t < pl.n_tiles; ++t) {
+                const uint64_t a_base = ptx::smem_desc(act[cur], pl.plane, 128);
+                const uint64_t b_base =
+                    ptx::smem_desc(ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0)), C * 16, 128);
+                uint32_t offs[9];
+#pragma unroll
+                for (int o = 0; o < 9; ++o)
+                    offs[o] = (uint32_t)(pl.r0 + ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * G);   // row of tile 0
+                for (int t = warp; t < pl.n_tiles; t += kIssuers) {
                     const uint32_t d = tmem + (uint32_t)(t * C);
-                    int first = 1;
+#pragma unroll
                     for (int o = 0; o < 9; ++o) {
-                        const int off = (o / 3 - 1) * Lp + (o % 3 - 1);
-                        const uint32_t arow = (uint32_t)(pl.r0 + t * 128 + off * G);
+                        const uint32_t arow = offs[o] + (uint32_t)(t * 128);
 #pragma unroll
                         for (int kk = 0; kk < C / 16; ++kk) {
-                            const uint64_t ad = ptx::smem_desc(a0 + (2 * kk) * pl.plane + arow * 16u, pl.plane, 128);
-                            const uint64_t bd = ptx::smem_desc(wb + (uint32_t)((o * (C / 8) + 2 * kk) * C * 16), C * 16, 128);
-                            ptx::mma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
-                            first = 0;
+                            const uint64_t ad = a_base + ((arow * 16u + (uint32_t)(2 * kk) * pl.plane) >> 4);
+                            const uint64_t bd = b_base + (uint64_t)(((o * (C / 8) + 2 * kk) * C * 16) >> 4);
+                            ptx::mma_bf16(d, ad, bd, idesc, (o | kk) ? 1u : 0u);
                         }
                     }
+                    ptx::mma_commit(&sh.bar_tile[t]);
                 }
-                ptx::mma_commit(sh.bar_mma);
             } else {
                 atomicOr(sh.abort_flag, 1);
                 atomicOr(err, ERRBIT_TIMEOUT);
@@ -191,24 +229,19 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
         }
         st.wseq += 1;
         st.wissued = st.wseq + 1;
-        // every thread waits for the layer's MMAs
-        const bool ok = ptx::mbar_wait(sh.bar_mma, st.mma_phase);
-        st.mma_phase ^= 1u;
-        if (!ok) {
-            atomicOr(sh.abort_flag, 1);
-            atomicOr(err, ERRBIT_TIMEOUT);
-        }
-        __syncthreads();
-        if (*sh.abort_flag) return false;
-        ptx::tc_fence_after();
+        st.layers += 1;
 
-        // epilogue: bias + SiLU; bf16 rows (and halo images) or head contributions
+        // epilogue per tile as soon as its MMAs complete: bias + SiLU; bf16
+        // rows (and halo images) or head contributions
         const float *bias = sh.f32 + 9 * pl.c_in * C + l * C;
         const float *wa = sh.f32 + 9 * pl.c_in * C + pl.n_layers * C;
         const uint32_t out = act[cur ^ 1];
         float *contrib = reinterpret_cast<float *>(sh.base + (cur ? pl.o_act0 : pl.o_act1));
-        const int quarter = warp & 3;
+        bool ok = true;
         for (int t = warp >> 2; t < pl.n_tiles; t += kTcThreads / 128) {
+            const bool got = wait_or_abort(&sh.bar_tile[t], parity, sh.abort_flag);
+            if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // reconverges the warp
+            ptx::tc_fence_after();
             float v[C];
 #pragma unroll
             for (int h = 0; h < C / 16; ++h) {
@@ -217,16 +250,16 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[16 * h + i] = tmp[i];
             }
-            const int row = pl.r0 + t * 128 + quarter * 32 + lane;
-            const int p = row / G, g = row - p * G;
-            const int y = p / Lp - 1, x = p % Lp - 1;
-            if (row >= pl.r0 + pl.count_out * G || x < 0 || x >= L || y < 0 || y >= L) continue;
+            const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
+            const uint32_t main = dst.x & 0xFFFFu;
+            if (main == kNone) continue;
             if (!last) {
                 uint32_t w[C / 2];
 #pragma unroll
                 for (int c = 0; c < C / 2; ++c)
-                    w[c] = ptx::pack_bf16(ptx::silu_fast(v[2 * c] + bias[2 * c]), ptx::silu_fast(v[2 * c + 1] + bias[2 * c + 1]));
-                store_row_images<C>(pl, out, x, y, g, w);
+                    w[c] = ptx::pack_bf16(ptx::silu_fast(v[2 * c] + bias[2 * c]),
+                                          ptx::silu_fast(v[2 * c + 1] + bias[2 * c + 1]));
+                store_rows<C>(pl, out, dst, w);
             } else {
                 float ca = 0.f, cp = 0.f;
 #pragma unroll
@@ -235,24 +268,29 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
                     ca = fmaf(wa[c], hv, ca);
                     cp = fmaf(wa[C + c], hv, cp);
                 }
-                const int site = y * L + x;
-                contrib[2 * (site * G + g)] = ca;
-                contrib[2 * (site * G + g) + 1] = cp;
+                contrib[2 * main] = ca;       // indexed by the row p * G + g
+                contrib[2 * main + 1] = cp;
             }
+        }
+        if (!ok) {
+            atomicOr(sh.abort_flag, 1);
+            atomicOr(err, ERRBIT_TIMEOUT);
         }
         ptx::tc_fence_before();
         ptx::fence_async_smem();
         __syncthreads();
+        if (*sh.abort_flag) return false;
         cur ^= 1;
     }
-    // head: a[g] = sum over sites of the contributions (one warp per g, fixed
-    // order); after the last swap the contributions sit in buffer `cur`
+    // head: a[g] = sum over sites of the contributions (one warp per g,
+    // fixed order); after the last swap the contributions sit in buffer `cur`
     const float *contrib = reinterpret_cast<const float *>(sh.base + (cur ? pl.o_act1 : pl.o_act0));
     for (int g = warp; g < G; g += kTcThreads / 32) {
         float sa = 0.f, sp = 0.f;
         for (int site = lane; site < pl.N; site += 32) {
-            sa += contrib[2 * (site * G + g)];
-            sp += contrib[2 * (site * G + g) + 1];
+            const int row = (int)(sh.sitetab[site].x & 0xFFFFu) * G + g;
+            sa += contrib[2 * row];
+            sp += contrib[2 * row + 1];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -260,8 +298,8 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
             sp += __shfl_xor_sync(0xffffffffu, sp, o);
         }
         if (lane == 0) {
-            sh.res.a[g] = (double)sa;
-            sh.res.phi[g] = (double)sp;
+            sh.a[g] = (double)sa;
+            sh.phi[g] = (double)sp;
         }
     }
     __syncthreads();
@@ -272,29 +310,53 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
 __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, const unsigned char *packed,
                          TcState &st) {
     sh.base = smem;
-    sh.bar_mma = reinterpret_cast<uint64_t *>(smem + pl.o_bar);
-    sh.bar_w = sh.bar_mma + 1;
-    sh.tmem_addr = reinterpret_cast<uint32_t *>(smem + pl.o_bar + 24);
-    sh.abort_flag = reinterpret_cast<int *>(smem + pl.o_bar + 28);
+    sh.bar_w = reinterpret_cast<uint64_t *>(smem + pl.o_bar);
+    sh.bar_tile = sh.bar_w + 2;
+    sh.tmem_addr = reinterpret_cast<uint32_t *>(smem + pl.o_bar + 8 * (2 + kMaxTiles));
+    sh.abort_flag = reinterpret_cast<int *>(smem + pl.o_bar + 8 * (2 + kMaxTiles) + 4);
     sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
+    sh.spad = reinterpret_cast<int8_t *>(smem + pl.o_spad);
+    sh.rowtab = reinterpret_cast<const uint2 *>(smem + pl.o_rowtab);
+    sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
     sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
-    sh.res.a = reinterpret_cast<double *>(smem + pl.o_res);
-    sh.res.phi = sh.res.a + pl.G;
+    sh.a = reinterpret_cast<double *>(smem + pl.o_res);
+    sh.phi = sh.a + pl.G;
     if (threadIdx.x == 0) {
-        ptx::mbar_init(sh.bar_mma, 1);
         ptx::mbar_init(&sh.bar_w[0], 1);
         ptx::mbar_init(&sh.bar_w[1], 1);
+        for (int t = 0; t < kMaxTiles; ++t) ptx::mbar_init(&sh.bar_tile[t], 1);
         *sh.abort_flag = 0;
         ptx::fence_mbar_init();
     }
     const float *src = reinterpret_cast<const float *>(packed);
     for (uint32_t i = threadIdx.x; i < pl.f32_count; i += blockDim.x) sh.f32[i] = src[i];
-    // zero both activation buffers once: rows outside the lattice are read
-    // by discarded output rows only, but keep them finite
+    // destination table of every output row: main row and periodic images
+    uint2 *rowtab = reinterpret_cast<uint2 *>(smem + pl.o_rowtab);
+    for (int lr = threadIdx.x; lr < pl.n_tiles * 128; lr += blockDim.x) {
+        const int row = pl.r0 + lr;
+        int pos[4];
+        int n = 0;
+        const int p = row / pl.G, g = row - p * pl.G;
+        const int y = p / pl.Lp - 1, x = p % pl.Lp - 1;
+        if (row < pl.r0 + pl.count_out * pl.G && x >= 0 && x < pl.L && y >= 0 && y < pl.L) {
+            n = images(pl.L, pl.Lp, x, y, pos);
+            for (int i = 0; i < n; ++i) pos[i] = pos[i] * pl.G + g;
+        }
+        rowtab[lr] = pack4(pos, n);
+    }
+    uint2 *sitetab = reinterpret_cast<uint2 *>(smem + pl.o_sitetab);
+    for (int s = threadIdx.x; s < pl.N; s += blockDim.x) {
+        int pos[4];
+        const int n = images(pl.L, pl.Lp, s % pl.L, s / pl.L, pos);
+        sitetab[s] = pack4(pos, n);
+    }
+    // zero both activation buffers and the padded spins once: rows outside
+    // the lattice are read by discarded output rows only, but keep them finite
     for (uint32_t i = threadIdx.x; i < pl.act_bytes / 4; i += blockDim.x) {
         reinterpret_cast<uint32_t *>(smem + pl.o_act0)[i] = 0u;
         reinterpret_cast<uint32_t *>(smem + pl.o_act1)[i] = 0u;
     }
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(pl.Lp * pl.Lp * pl.G); i += blockDim.x) sh.spad[i] = 0;
     ptx::fence_async_smem();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
@@ -302,7 +364,7 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
         ptx::tmem_relinquish();
     }
     if (threadIdx.x == 0) issue_weight_load(pl, sh, packed, 0);
-    st.mma_phase = 0;
+    st.layers = 0;
     st.wseq = 0;
     st.wissued = 1;
     ptx::tc_fence_before();
@@ -343,8 +405,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) logpsi_tc_kernel(TcPlan pl, con
         __syncthreads();
         if (!tc_group_forward<C>(pl, sh, packed, st, err)) break;
         for (int g = threadIdx.x; g < gc; g += blockDim.x) {
-            out[2 * (b0 + g)] = sh.res.a[g];
-            out[2 * (b0 + g) + 1] = sh.res.phi[g];
+            out[2 * (b0 + g)] = sh.a[g];
+            out[2 * (b0 + g) + 1] = sh.phi[g];
         }
         __syncthreads();
     }
@@ -368,18 +430,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Probl
     int *cum = reinterpret_cast<int *>(ch + p.n_bonds);
     EnumScratch *scr = reinterpret_cast<EnumScratch *>(ex + al16(N) + al16(4 * p.n_bonds) + al16(8 * p.n_bonds) +
                                                        al16(4 * (N + 1)));
-    double *ref = reinterpret_cast<double *>(scr + 1);   // a0, phi0, sum re, sum im
+    double *ref = reinterpret_cast<double *>(scr + 1);   // a0, phi0
+    double *lp = ref + 4;                                 // [n_bonds + 1][2]: (a, phi) of every list entry
     const int recompute = logpsi == nullptr;
     for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
         for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = configs[s * N + r];
         __syncthreads();
         double hd;
         const int nconn = enumerate_connected(p, sigma, ci, cj, ch, &hd, cum, *scr);
-        if (threadIdx.x == 0) {
-            ref[2] = 0.0;
-            ref[3] = 0.0;
-            if (!recompute) { ref[0] = logpsi[2 * s]; ref[1] = logpsi[2 * s + 1]; }
-        }
+        if (threadIdx.x == 0 && !recompute) { ref[0] = logpsi[2 * s]; ref[1] = logpsi[2 * s + 1]; }
         __syncthreads();
         const int n_entries = nconn + recompute;
         bool ok = true;
@@ -398,26 +457,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Probl
             }
             __syncthreads();
             if (!tc_group_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
-            if (threadIdx.x == 0) {
-                if (e0 == 0 && recompute) { ref[0] = sh.res.a[0]; ref[1] = sh.res.phi[0]; }
-                double sr = ref[2], si = ref[3];
-                for (int g = 0; g < gc; ++g) {   // terms added in list order
-                    const int k = e0 + g - recompute;
-                    if (k < 0) continue;
-                    const double m = ch[k] * exp(sh.res.a[g] - ref[0]);
-                    double sn, cs;
-                    sincos(sh.res.phi[g] - ref[1], &sn, &cs);
-                    sr += m * cs;
-                    si += m * sn;
-                }
-                ref[2] = sr;
-                ref[3] = si;
+            if (threadIdx.x < gc) {
+                lp[2 * (e0 + threadIdx.x)] = sh.a[threadIdx.x];
+                lp[2 * (e0 + threadIdx.x) + 1] = sh.phi[threadIdx.x];
             }
-            __syncthreads();
         }
         if (!ok) break;
+        __syncthreads();
+        if (recompute && threadIdx.x == 0) { ref[0] = lp[0]; ref[1] = lp[1]; }
+        __syncthreads();
+        // E_loc = H_diag + sum_k H_k exp((a'_k - a) + i (phi'_k - phi)) in float64,
+        // all terms of the sample at once, fixed-order block reduction
+        double tr = 0.0, ti = 0.0;
+        for (int k = threadIdx.x; k < nconn; k += blockDim.x) {
+            const double m = ch[k] * exp(lp[2 * (k + recompute)] - ref[0]);
+            double sn, cs;
+            sincos(lp[2 * (k + recompute) + 1] - ref[1], &sn, &cs);
+            tr = fma(m, cs, tr);
+            ti = fma(m, sn, ti);
+        }
+        const double sr = block_sum(tr, scr->dscr);
+        const double si = block_sum(ti, scr->dscr);
         if (threadIdx.x == 0) {
-            const double er = hd + ref[2], ei = ref[3];
+            const double er = hd + sr, ei = si;
             out[2 * s] = er;
             out[2 * s + 1] = ei;
             if (!isfinite(er) || !isfinite(ei)) atomicOr(err, ERRBIT_NONFINITE);
@@ -466,7 +528,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, con
         }
         __syncthreads();
         ok = tc_group_forward<C>(pl, sh, packed, st, err);
-        for (int g = threadIdx.x; g < gc; g += blockDim.x) { ca[g] = sh.res.a[g]; cphi[g] = sh.res.phi[g]; }
+        for (int g = threadIdx.x; g < gc; g += blockDim.x) { ca[g] = sh.a[g]; cphi[g] = sh.phi[g]; }
         __syncthreads();
     }
     const int n_sweeps = burn_in + spc * sweeps_between;
@@ -501,14 +563,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, con
             if (!tc_group_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
             for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
                 const int g = list[m];
-                const double delta = 2.0 * (sh.res.a[m] - ca[g]);
+                const double delta = 2.0 * (sh.a[m] - ca[g]);
                 if (delta >= 0.0 || pu[g] < exp(delta)) {
                     const int i = pi[g], j = pj[g];
                     const int8_t t = cur[g * N + i];
                     cur[g * N + i] = cur[g * N + j];
                     cur[g * N + j] = t;
-                    ca[g] = sh.res.a[m];
-                    cphi[g] = sh.res.phi[m];
+                    ca[g] = sh.a[m];
+                    cphi[g] = sh.phi[m];
                 }
             }
             __syncthreads();
@@ -590,9 +652,12 @@ bool make_plan(const Problem &p, int G, size_t max_smem, int extra_bytes, TcPlan
     pl.o_w0 = o; o = al16(o + pl.wbytes);
     pl.o_w1 = o; o = al16(o + pl.wbytes);
     pl.o_f32 = o; o = al16(o + pl.f32_count * 4);
+    pl.o_rowtab = o; o = al16(o + 8 * pl.n_tiles * 128);
+    pl.o_sitetab = o; o = al16(o + 8 * p.N);
+    pl.o_spad = o; o = al16(o + pl.Lp * pl.Lp * G);
     pl.o_spins = o; o = al16(o + G * p.N);
     pl.o_res = o; o = al16(o + 16 * G);
-    pl.o_bar = o; o = al16(o + 32);
+    pl.o_bar = o; o = al16(o + 8 * (2 + kMaxTiles) + 8);
     pl.o_extra = o; o = al16(o + extra_bytes);
     // co-resident blocks must not ask for more than the SM's 512 TMEM
     // columns together: pad shared memory to cap residency
@@ -600,28 +665,30 @@ bool make_plan(const Problem &p, int G, size_t max_smem, int extra_bytes, TcPlan
     while (cols * (sm_bytes / (o + 1024u)) > 512u) o += 1024u;
     pl.total = o;
     if (cols > 512) { *why = "tensor-memory tile does not fit in 512 columns"; return false; }
+    if (pl.n_tiles > kMaxTiles) { *why = "more than 16 row tiles per group"; return false; }
+    if (pl.rbuf >= (int)kNone) { *why = "row index range exceeds 16 bits"; return false; }
     if (pl.total > max_smem) { *why = "shared memory plan exceeds the per-block limit"; return false; }
     if (pl.n_tc < 1) { *why = "the tensor-core path needs at least two conv layers"; return false; }
     *out = pl;
     return true;
 }
 
-int eloc_extra(const Problem &p) {
+int eloc_extra(const Problem &p, int G) {
+    (void)G;
     return (int)(al16(p.N) + al16(4 * p.n_bonds) + al16(8 * p.n_bonds) + al16(4 * (p.N + 1)) + sizeof(EnumScratch) +
-                 4 * sizeof(double));
+                 4 * sizeof(double) + 16 * (p.n_bonds + 1));
 }
 
 int sample_extra(const Problem &p, int G) { return (int)(al16(G * p.N) + al16(4 * (3 * G + 1)) + 24 * G); }
 
 // Choose G maximising useful rows / computed rows within the limits.
-bool best_plan(const Problem &p, size_t max_smem, int extra_fixed, int extra_per_g, int gmax, TcPlan *out,
-               std::string *why) {
+bool best_plan(const Problem &p, size_t max_smem, bool eloc, int gmax, TcPlan *out, std::string *why) {
     double best = -1.0;
     bool found = false;
     for (int G = 1; G <= gmax; ++G) {
         TcPlan pl;
         std::string w;
-        if (!make_plan(p, G, max_smem, extra_fixed + extra_per_g * G, &pl, &w)) { if (!found) *why = w; continue; }
+        if (!make_plan(p, G, max_smem, eloc ? eloc_extra(p, G) : 0, &pl, &w)) { if (!found) *why = w; continue; }
         const double eff = (double)(p.N * G) / (double)(pl.n_tiles * 128);
         if (eff > best + 1e-9) { best = eff; *out = pl; found = true; }
     }
@@ -686,7 +753,7 @@ int launch_logpsi_tc(const Problem &p, const double *, const void *packed, const
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
-    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, 0, 0, 16, &pl, &why)) {
+    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, false, 16, &pl, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
@@ -705,7 +772,7 @@ int launch_eloc_tc(const Problem &p, const double *, const void *packed, const i
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
-    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, eloc_extra(p), 0, 16, &pl, &why)) {
+    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, &pl, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
