@@ -11,15 +11,21 @@
 // the same matrix shifted by ((dy (L + 2) + dx) * G) rows, so each tap is
 // one tcgen05.mma whose A descriptor starts at a shifted address (an
 // implicit GEMM with no im2col copy): M = 128 rows, N = C, K = 16.
-// Halo rows are refreshed by the epilogue, which writes every interior
-// output also to its periodic images (a per-row destination table built
-// once per kernel). Weights of the next layer stream in by bulk copy (TMA)
-// while the current layer computes. Each 128-row tile commits to its own
-// mbarrier, so the epilogue of tile t overlaps the MMAs of later tiles.
-// Layer 0 (one spin channel or three one-hot channels) runs on CUDA cores
-// in fp32 from a padded copy of the spins.
+// Layer 0 (one spin channel, or three one-hot channels) instead reads a
+// small im2col matrix of the spins (K = 16 or 32).
+//
+// Pipeline. Halo rows are refreshed by the epilogue, which writes every
+// interior output also to its periodic images (a per-row destination table
+// built once per kernel). Each 128-row tile commits to its own mbarrier, so
+// the epilogue of tile t overlaps the MMAs of later tiles; two dedicated
+// warps issue the MMAs while eight warps run epilogues. Two groups ("slots") are in
+// flight: while the CUDA cores run the epilogue of one slot's layer, the
+// tensor core runs the other slot's MMAs. The next layer's weights stream
+// in by bulk copy (TMA) into a double buffer while the current layer runs.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include <cuda_bf16.h>
 
@@ -30,20 +36,22 @@ namespace nqs {
 
 namespace {
 
-constexpr int kTcThreads = 256;   // 8 warps: warp w reads TMEM lanes 32 (w % 4) ...; tiles split by w / 4
+constexpr int kEpiWarps = 8;      // epilogue warps: warp w reads TMEM lanes 32 (w % 4) ...; tiles split by w / 4
+constexpr int kIssuers = 2;       // dedicated issuing warps (lane 0 issues tcgen05.mma), after the epilogue warps
+constexpr int kTcThreads = 32 * (kEpiWarps + kIssuers);
 constexpr int kMaxTiles = 16;
-constexpr int kIssuers = 4;       // threads issuing tcgen05.mma (lane 0 of warps 0..3)
+constexpr int kMaxSlots = 2;
 constexpr uint32_t kNone = 0xFFFFu;
 
 struct TcPlan {
-    int L, Lp, N, G, C, KC, c_in, n_layers, n_tc;
+    int L, Lp, N, G, C, KC, c_in, K0, n_layers, slots;
     int count_out, n_tiles, r0, rbuf;
-    uint32_t plane, act_bytes, wbytes, tmem_cols;
-    // packed parameter image (global): fp32 block then one bf16 block per tensor-core layer
-    uint32_t f32_count;    // 9 c_in C + n_layers C + 2 C floats
-    uint32_t f32_bytes;    // padded to 16
-    // shared-memory offsets
-    uint32_t o_act0, o_act1, o_w0, o_w1, o_f32, o_rowtab, o_sitetab, o_spad, o_spins, o_res, o_bar, o_extra, total;
+    uint32_t plane, act_bytes, w0bytes, wbytes, tmem_cols, slot_cols;
+    // packed parameter image (global): fp32 biases + head, then bf16 operand
+    // images of layer 0 (K0 x C) and of every later layer (9 x C x C)
+    uint32_t f32_count, f32_bytes;
+    // shared-memory offsets; act holds slots x 2 buffers of act_bytes
+    uint32_t o_act, o_w0, o_w1, o_f32, o_rowtab, o_sitetab, o_spad, o_spins, o_res, o_bar, o_extra, total;
 };
 
 __host__ __device__ inline uint32_t al16(uint32_t v) { return (v + 15u) & ~15u; }
@@ -51,35 +59,40 @@ __host__ __device__ inline uint32_t al16(uint32_t v) { return (v + 15u) & ~15u; 
 struct TcShared {
     unsigned char *base;
     uint64_t *bar_w;             // [2] weight buffers
-    uint64_t *bar_tile;          // [kMaxTiles] per-tile MMA completion
+    uint64_t *bar_tile;          // [slots][kMaxTiles] per-tile MMA completion
     uint32_t *tmem_addr;
     int *abort_flag;
-    int8_t *spins;               // [G][N] the group's configurations
-    int8_t *spad;                // [Lp * Lp * G] padded copy, row = pos * G + g
+    int8_t *spins;               // [slots][G][N] the groups' configurations
+    int8_t *spad;                // [slots][Lp * Lp * G] padded copies, row = pos * G + g
     const uint2 *rowtab;         // [n_tiles * 128] destination rows of each output row
     const uint2 *sitetab;        // [N] padded positions of each site (main + images)
-    float *f32;                  // w0s [9][c_in][C], biases [n_layers][C], head [2][C]
-    double *a, *phi;             // [G] results
+    float *f32;                  // biases [n_layers][C], head [2][C]
+    double *res;                 // [slots][2][G]: a, then phi
 };
 
 struct TcState {        // per-CTA pipeline state (all threads keep identical copies)
-    uint32_t layers;    // tensor-core layers executed so far (tile-barrier parity)
-    uint32_t wseq;      // weight loads consumed so far
-    uint32_t wissued;   // weight loads issued so far
+    uint32_t layers[kMaxSlots];   // layers completed per slot (tile-barrier parity)
+    uint32_t wseq;                // weight load used by the next forward's layer 0
+    uint32_t wissued;             // weight loads issued so far
 };
 
-__device__ __forceinline__ const unsigned char *tc_layer_weights(const TcPlan &pl, const unsigned char *packed, int l) {
-    return packed + pl.f32_bytes + (size_t)(l - 1) * pl.wbytes;
+__device__ __forceinline__ uint32_t act_addr(const TcPlan &pl, const TcShared &sh, int slot, int b) {
+    return ptx::smem_u32(sh.base + pl.o_act + (uint32_t)(slot * 2 + b) * pl.act_bytes);
 }
 
-// Issue the bulk copy of weight-load number q (tensor-core layer 1 + q mod n_tc).
+__device__ __forceinline__ const unsigned char *tc_layer_weights(const TcPlan &pl, const unsigned char *packed, int l) {
+    return packed + pl.f32_bytes + (l == 0 ? 0 : pl.w0bytes + (size_t)(l - 1) * pl.wbytes);
+}
+
+// Issue the bulk copy of weight-load number q (layer q mod n_layers).
 __device__ __forceinline__ void issue_weight_load(const TcPlan &pl, const TcShared &sh, const unsigned char *packed,
                                                   uint32_t q) {
-    const int l = 1 + (int)(q % (uint32_t)pl.n_tc);
+    const int l = (int)(q % (uint32_t)pl.n_layers);
     const int b = q & 1;
+    const uint32_t bytes = l == 0 ? pl.w0bytes : pl.wbytes;
     unsigned char *dst = sh.base + (b ? pl.o_w1 : pl.o_w0);
-    ptx::mbar_arrive_expect_tx(&sh.bar_w[b], pl.wbytes);
-    ptx::bulk_g2s(dst, tc_layer_weights(pl, packed, l), pl.wbytes, &sh.bar_w[b]);
+    ptx::mbar_arrive_expect_tx(&sh.bar_w[b], bytes);
+    ptx::bulk_g2s(dst, tc_layer_weights(pl, packed, l), bytes, &sh.bar_w[b]);
 }
 
 // Wait on an mbarrier phase; gives up when another thread raised the abort
@@ -90,6 +103,11 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, co
         if ((it & 255) == 255 && *(volatile const int *)abort_flag) return false;
     }
     return false;
+}
+
+__device__ __forceinline__ void raise_abort(const TcShared &sh, int *err) {
+    atomicOr(sh.abort_flag, 1);
+    atomicOr(err, ERRBIT_TIMEOUT);
 }
 
 // Padded positions holding interior site (x, y) and its periodic images.
@@ -124,91 +142,88 @@ __device__ __forceinline__ void store_rows(const TcPlan &pl, uint32_t act, uint2
     }
 }
 
-// Layer 0 on CUDA cores: input channels from the padded spins, fp32 weights.
-// Each thread handles the same output rows as in the tensor-core epilogue.
-template <int C>
-__device__ void layer0(const TcPlan &pl, const TcShared &sh, uint32_t act_out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
-    const float *w0 = sh.f32;                         // [9][c_in][C]
-    const float *b0 = sh.f32 + 9 * pl.c_in * C;       // bias of layer 0
-    int offg[9];
-#pragma unroll
-    for (int o = 0; o < 9; ++o) offg[o] = ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * pl.G;
-    for (int t = warp >> 2; t < pl.n_tiles; t += kTcThreads / 128) {
-        const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
-        const uint32_t main = dst.x & 0xFFFFu;
-        if (main == kNone) continue;
-        float z[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) z[c] = b0[c];
-#pragma unroll
-        for (int o = 0; o < 9; ++o) {
-            const int s = sh.spad[(int)main + offg[o]];
-            if (pl.c_in == 1) {
-                const float fs = (float)s;
-                const float *wr = w0 + o * C;
-#pragma unroll
-                for (int c = 0; c < C; ++c) z[c] = fmaf(wr[c], fs, z[c]);
-            } else {
-                const int ch = s == 0 ? 0 : (s == 1 ? 1 : 2);
-                const float *wr = w0 + (o * 3 + ch) * C;
-#pragma unroll
-                for (int c = 0; c < C; ++c) z[c] += wr[c];
-            }
-        }
-        uint32_t w[C / 2];
-#pragma unroll
-        for (int c = 0; c < C / 2; ++c) w[c] = ptx::pack_bf16(ptx::silu_fast(z[2 * c]), ptx::silu_fast(z[2 * c + 1]));
-        store_rows<C>(pl, act_out, dst, w);
-    }
-}
-
-// Evaluate the G configurations in sh.spins; results to sh.a / sh.phi
-// (double). Returns false if a wait timed out (the block must stop).
-template <int C>
-__device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st,
-                                 int *err) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
-    const uint32_t act[2] = {ptx::smem_u32(sh.base + pl.o_act0), ptx::smem_u32(sh.base + pl.o_act1)};
-    const uint32_t tmem = *sh.tmem_addr;
-    const uint32_t idesc = ptx::idesc_bf16(128, C);
+// Spins of a slot to the padded lattice, then the layer-0 im2col matrix
+// (row = output row, K0 columns: tap-major, one-hot channel minor; zero
+// padded) into the slot's second activation buffer.
+__device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot) {
     const int G = pl.G;
-
-    // padded spins: every site to its main position and periodic images
+    int8_t *spad = sh.spad + slot * pl.Lp * pl.Lp * G;
+    const int8_t *spins = sh.spins + slot * G * pl.N;
     for (int r = threadIdx.x; r < G * pl.N; r += blockDim.x) {
         const int g = r / pl.N, site = r - g * pl.N;
         const uint2 pos = sh.sitetab[site];
-        const int8_t v = sh.spins[r];
+        const int8_t v = spins[r];
         const uint32_t d[4] = {pos.x & 0xFFFFu, pos.x >> 16, pos.y & 0xFFFFu, pos.y >> 16};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            if (d[i] != kNone) sh.spad[d[i] * G + g] = v;
+            if (d[i] != kNone) spad[d[i] * G + g] = v;
     }
     __syncthreads();
-    layer0<C>(pl, sh, act[0]);
+    int offg[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) offg[o] = ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * G;
+    const uint32_t a0 = act_addr(pl, sh, slot, 1);
+    const uint32_t one = 0x3F80u, minus_one = 0xBF80u;   // bf16 +1, -1
+    for (int lr = threadIdx.x; lr < pl.n_tiles * 128; lr += blockDim.x) {
+        const uint32_t main = sh.rowtab[lr].x & 0xFFFFu;
+        const uint32_t row = (uint32_t)(pl.r0 + lr);
+        uint32_t w[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w[i] = 0u;
+        if (main != kNone) {
+#pragma unroll
+            for (int o = 0; o < 9; ++o) {
+                const int s = spad[(int)main + offg[o]];
+                if (pl.c_in == 1) {
+                    const uint32_t b = s > 0 ? one : minus_one;
+                    w[o >> 1] |= b << (16 * (o & 1));
+                } else {
+                    const int k = 3 * o + (s == 0 ? 0 : (s == 1 ? 1 : 2));
+                    w[k >> 1] |= one << (16 * (k & 1));
+                }
+            }
+        }
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc)
+            if (kc < pl.K0 / 8)
+                ptx::st_shared_v4(a0 + kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+    }
     ptx::fence_async_smem();
     __syncthreads();
+}
 
-    int cur = 0;
-    for (int l = 1; l < pl.n_layers; ++l) {
-        const bool last = (l == pl.n_layers - 1);
-        const uint32_t parity = st.layers & 1u;
-        // four issuing threads (lane 0 of warps 0-3, one per SM sub-partition),
-        // issuer w owns tiles w, w + 4, ...; each tile commits to its own barrier
-        if (lane == 0 && warp < kIssuers) {
-            const uint32_t q = st.wseq;
-            if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
-                // prefetch the next load into the other buffer (its last reader, load q - 1, has completed)
-                if (warp == 0) issue_weight_load(pl, sh, packed, q + 1);
-                ptx::tc_fence_after();
-                const uint64_t a_base = ptx::smem_desc(act[cur], pl.plane, 128);
-                const uint64_t b_base =
-                    ptx::smem_desc(ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0)), C * 16, 128);
+// Issue the MMAs of layer l for one slot (issuer threads only).
+template <int C>
+__device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int slot,
+                            int l, int *err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t q = st.wseq + (uint32_t)l;
+    const int iw = warp - kEpiWarps;   // issuer index
+    if (lane == 0 && iw >= 0) {
+        if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
+            // the last slot prefetches the next load into the other buffer:
+            // its previous user (load q - 1) has completed for every slot
+            if (iw == 0 && slot == pl.slots - 1) issue_weight_load(pl, sh, packed, q + 1);
+            ptx::tc_fence_after();
+            const uint32_t tmem = *sh.tmem_addr + (uint32_t)(slot * pl.slot_cols);
+            const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
+            const uint64_t b_base = ptx::smem_desc(wb, C * 16, 128);
+            const uint32_t idesc = ptx::idesc_bf16(128, C);
+            if (l == 0) {
+                const uint64_t a_base = ptx::smem_desc(act_addr(pl, sh, slot, 1), pl.plane, 128);
+                for (int t = iw; t < pl.n_tiles; t += kIssuers) {
+                    const uint32_t arow = (uint32_t)(pl.r0 + t * 128);
+                    for (int kk = 0; kk < pl.K0 / 16; ++kk)
+                        ptx::mma_bf16(tmem + (uint32_t)(t * C), a_base + ((arow * 16u + (uint32_t)(2 * kk) * pl.plane) >> 4),
+                                      b_base + (uint64_t)((2 * kk * C * 16) >> 4), idesc, kk ? 1u : 0u);
+                    ptx::mma_commit(&sh.bar_tile[slot * kMaxTiles + t]);
+                }
+            } else {
+                const uint64_t a_base = ptx::smem_desc(act_addr(pl, sh, slot, (l - 1) & 1), pl.plane, 128);
                 uint32_t offs[9];
 #pragma unroll
-                for (int o = 0; o < 9; ++o)
-                    offs[o] = (uint32_t)(pl.r0 + ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * G);   // row of tile 0
-                for (int t = warp; t < pl.n_tiles; t += kIssuers) {
+                for (int o = 0; o < 9; ++o) offs[o] = (uint32_t)(pl.r0 + ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * pl.G);
+                for (int t = iw; t < pl.n_tiles; t += kIssuers) {
                     const uint32_t d = tmem + (uint32_t)(t * C);
 #pragma unroll
                     for (int o = 0; o < 9; ++o) {
@@ -220,71 +235,77 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
                             ptx::mma_bf16(d, ad, bd, idesc, (o | kk) ? 1u : 0u);
                         }
                     }
-                    ptx::mma_commit(&sh.bar_tile[t]);
+                    ptx::mma_commit(&sh.bar_tile[slot * kMaxTiles + t]);
                 }
-            } else {
-                atomicOr(sh.abort_flag, 1);
-                atomicOr(err, ERRBIT_TIMEOUT);
             }
+        } else {
+            raise_abort(sh, err);
         }
-        st.wseq += 1;
-        st.wissued = st.wseq + 1;
-        st.layers += 1;
-
-        // epilogue per tile as soon as its MMAs complete: bias + SiLU; bf16
-        // rows (and halo images) or head contributions
-        const float *bias = sh.f32 + 9 * pl.c_in * C + l * C;
-        const float *wa = sh.f32 + 9 * pl.c_in * C + pl.n_layers * C;
-        const uint32_t out = act[cur ^ 1];
-        float *contrib = reinterpret_cast<float *>(sh.base + (cur ? pl.o_act0 : pl.o_act1));
-        bool ok = true;
-        for (int t = warp >> 2; t < pl.n_tiles; t += kTcThreads / 128) {
-            const bool got = wait_or_abort(&sh.bar_tile[t], parity, sh.abort_flag);
-            if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // reconverges the warp
-            ptx::tc_fence_after();
-            float v[C];
-#pragma unroll
-            for (int h = 0; h < C / 16; ++h) {
-                float tmp[16];
-                ptx::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * C + 16 * h), tmp);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[16 * h + i] = tmp[i];
-            }
-            const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
-            const uint32_t main = dst.x & 0xFFFFu;
-            if (main == kNone) continue;
-            if (!last) {
-                uint32_t w[C / 2];
-#pragma unroll
-                for (int c = 0; c < C / 2; ++c)
-                    w[c] = ptx::pack_bf16(ptx::silu_fast(v[2 * c] + bias[2 * c]),
-                                          ptx::silu_fast(v[2 * c + 1] + bias[2 * c + 1]));
-                store_rows<C>(pl, out, dst, w);
-            } else {
-                float ca = 0.f, cp = 0.f;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const float hv = ptx::silu_fast(v[c] + bias[c]);
-                    ca = fmaf(wa[c], hv, ca);
-                    cp = fmaf(wa[C + c], hv, cp);
-                }
-                contrib[2 * main] = ca;       // indexed by the row p * G + g
-                contrib[2 * main + 1] = cp;
-            }
-        }
-        if (!ok) {
-            atomicOr(sh.abort_flag, 1);
-            atomicOr(err, ERRBIT_TIMEOUT);
-        }
-        ptx::tc_fence_before();
-        ptx::fence_async_smem();
-        __syncthreads();
-        if (*sh.abort_flag) return false;
-        cur ^= 1;
     }
-    // head: a[g] = sum over sites of the contributions (one warp per g,
-    // fixed order); after the last swap the contributions sit in buffer `cur`
-    const float *contrib = reinterpret_cast<const float *>(sh.base + (cur ? pl.o_act1 : pl.o_act0));
+    if (slot == pl.slots - 1) st.wissued = q + 2;
+}
+
+// Epilogue of layer l for one slot: per tile as soon as its MMAs complete,
+// bias + SiLU, then bf16 rows (and halo images) or, after the last layer,
+// head contributions. Ends with a block barrier. False on abort.
+template <int C>
+__device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st, int slot, int l, int *err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
+    const bool last = l == pl.n_layers - 1;
+    const uint32_t parity = st.layers[slot] & 1u;
+    const uint32_t tmem = *sh.tmem_addr + (uint32_t)(slot * pl.slot_cols);
+    const float *bias = sh.f32 + l * C;
+    const float *wa = sh.f32 + pl.n_layers * C;
+    const uint32_t out = act_addr(pl, sh, slot, l & 1);
+    float *contrib = reinterpret_cast<float *>(sh.base + pl.o_act + (uint32_t)(slot * 2 + (l & 1)) * pl.act_bytes);
+    bool ok = true;
+    for (int t = warp >> 2; warp < kEpiWarps && t < pl.n_tiles; t += kEpiWarps / 4) {
+        const bool got = wait_or_abort(&sh.bar_tile[slot * kMaxTiles + t], parity, sh.abort_flag);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // reconverges the warp
+        ptx::tc_fence_after();
+        float v[C];
+#pragma unroll
+        for (int h = 0; h < C / 16; ++h) {
+            float tmp[16];
+            ptx::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * C + 16 * h), tmp);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[16 * h + i] = tmp[i];
+        }
+        const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
+        const uint32_t main = dst.x & 0xFFFFu;
+        if (main == kNone) continue;
+        if (!last) {
+            uint32_t w[C / 2];
+#pragma unroll
+            for (int c = 0; c < C / 2; ++c)
+                w[c] = ptx::pack_bf16(ptx::silu_fast(v[2 * c] + bias[2 * c]), ptx::silu_fast(v[2 * c + 1] + bias[2 * c + 1]));
+            store_rows<C>(pl, out, dst, w);
+        } else {
+            float ca = 0.f, cp = 0.f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float hv = ptx::silu_fast(v[c] + bias[c]);
+                ca = fmaf(wa[c], hv, ca);
+                cp = fmaf(wa[C + c], hv, cp);
+            }
+            contrib[2 * main] = ca;       // indexed by the row p * G + g
+            contrib[2 * main + 1] = cp;
+        }
+    }
+    if (!ok) raise_abort(sh, err);
+    st.layers[slot] += 1;
+    ptx::tc_fence_before();
+    ptx::fence_async_smem();
+    __syncthreads();
+    return *(volatile int *)sh.abort_flag == 0;
+}
+
+// a[g] = sum over sites of the head contributions (one warp per g, fixed order).
+__device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G;
+    const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act +
+                                                           (uint32_t)(slot * 2 + ((pl.n_layers - 1) & 1)) * pl.act_bytes);
+    double *res = sh.res + slot * 2 * G;
     for (int g = warp; g < G; g += kTcThreads / 32) {
         float sa = 0.f, sp = 0.f;
         for (int site = lane; site < pl.N; site += 32) {
@@ -298,11 +319,29 @@ __device__ bool tc_group_forward(const TcPlan &pl, const TcShared &sh, const uns
             sp += __shfl_xor_sync(0xffffffffu, sp, o);
         }
         if (lane == 0) {
-            sh.a[g] = (double)sa;
-            sh.phi[g] = (double)sp;
+            res[g] = (double)sa;
+            res[G + g] = (double)sp;
         }
     }
     __syncthreads();
+}
+
+// Evaluate every slot's G configurations (sh.spins); results in sh.res.
+// Returns false if a wait timed out (the block must stop).
+template <int C>
+__device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int *err) {
+    for (int s = 0; s < pl.slots; ++s) {
+        build_slot(pl, sh, s);
+        issue_layer<C>(pl, sh, packed, st, s, 0, err);
+    }
+    for (int l = 0; l < pl.n_layers; ++l) {
+        for (int s = 0; s < pl.slots; ++s) {
+            if (!epilogue_layer<C>(pl, sh, st, s, l, err)) return false;
+            if (l + 1 < pl.n_layers) issue_layer<C>(pl, sh, packed, st, s, l + 1, err);
+            else head_slot(pl, sh, s);
+        }
+    }
+    st.wseq += (uint32_t)pl.n_layers;
     return true;
 }
 
@@ -312,19 +351,18 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
     sh.base = smem;
     sh.bar_w = reinterpret_cast<uint64_t *>(smem + pl.o_bar);
     sh.bar_tile = sh.bar_w + 2;
-    sh.tmem_addr = reinterpret_cast<uint32_t *>(smem + pl.o_bar + 8 * (2 + kMaxTiles));
-    sh.abort_flag = reinterpret_cast<int *>(smem + pl.o_bar + 8 * (2 + kMaxTiles) + 4);
+    sh.tmem_addr = reinterpret_cast<uint32_t *>(smem + pl.o_bar + 8 * (2 + kMaxSlots * kMaxTiles));
+    sh.abort_flag = reinterpret_cast<int *>(smem + pl.o_bar + 8 * (2 + kMaxSlots * kMaxTiles) + 4);
     sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
     sh.spad = reinterpret_cast<int8_t *>(smem + pl.o_spad);
     sh.rowtab = reinterpret_cast<const uint2 *>(smem + pl.o_rowtab);
     sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
     sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
-    sh.a = reinterpret_cast<double *>(smem + pl.o_res);
-    sh.phi = sh.a + pl.G;
+    sh.res = reinterpret_cast<double *>(smem + pl.o_res);
     if (threadIdx.x == 0) {
         ptx::mbar_init(&sh.bar_w[0], 1);
         ptx::mbar_init(&sh.bar_w[1], 1);
-        for (int t = 0; t < kMaxTiles; ++t) ptx::mbar_init(&sh.bar_tile[t], 1);
+        for (int t = 0; t < kMaxSlots * kMaxTiles; ++t) ptx::mbar_init(&sh.bar_tile[t], 1);
         *sh.abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -350,13 +388,11 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
         const int n = images(pl.L, pl.Lp, s % pl.L, s / pl.L, pos);
         sitetab[s] = pack4(pos, n);
     }
-    // zero both activation buffers and the padded spins once: rows outside
-    // the lattice are read by discarded output rows only, but keep them finite
-    for (uint32_t i = threadIdx.x; i < pl.act_bytes / 4; i += blockDim.x) {
-        reinterpret_cast<uint32_t *>(smem + pl.o_act0)[i] = 0u;
-        reinterpret_cast<uint32_t *>(smem + pl.o_act1)[i] = 0u;
-    }
-    for (uint32_t i = threadIdx.x; i < (uint32_t)(pl.Lp * pl.Lp * pl.G); i += blockDim.x) sh.spad[i] = 0;
+    // zero the activation buffers and padded spins once: rows outside the
+    // lattice are read by discarded output rows only, but keep them finite
+    for (uint32_t i = threadIdx.x; i < pl.slots * 2 * pl.act_bytes / 4; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(smem + pl.o_act)[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(pl.slots * pl.Lp * pl.Lp * pl.G); i += blockDim.x) sh.spad[i] = 0;
     ptx::fence_async_smem();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
@@ -364,7 +400,7 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
         ptx::tmem_relinquish();
     }
     if (threadIdx.x == 0) issue_weight_load(pl, sh, packed, 0);
-    st.layers = 0;
+    for (int s = 0; s < kMaxSlots; ++s) st.layers[s] = 0;
     st.wseq = 0;
     st.wissued = 1;
     ptx::tc_fence_before();
@@ -375,7 +411,7 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
 __device__ void tc_teardown(const TcPlan &pl, TcShared &sh, TcState &st) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        // the prefetched weight load that nobody consumed
+        // prefetched weight loads that nobody consumed
         for (uint32_t q = st.wseq; q < st.wissued; ++q) ptx::mbar_wait(&sh.bar_w[q & 1], (q >> 1) & 1);
     }
     ptx::tc_fence_before();
@@ -395,18 +431,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) logpsi_tc_kernel(TcPlan pl, con
     TcShared sh;
     TcState st;
     tc_setup(pl, sh, smem, packed, st);
-    const int G = pl.G, N = pl.N;
-    for (int64_t b0 = (int64_t)blockIdx.x * G; b0 < n; b0 += (int64_t)gridDim.x * G) {
-        const int gc = (int)min((int64_t)G, n - b0);
-        for (int r = threadIdx.x; r < G * N; r += blockDim.x) {
-            const int g = r / N;
-            sh.spins[r] = configs[(b0 + (g < gc ? g : 0)) * N + (r - g * N)];
+    const int G = pl.G, N = pl.N, per = G * pl.slots;
+    for (int64_t b0 = (int64_t)blockIdx.x * per; b0 < n; b0 += (int64_t)gridDim.x * per) {
+        const int cnt = (int)min((int64_t)per, n - b0);
+        for (int r = threadIdx.x; r < per * N; r += blockDim.x) {
+            const int c = r / N;
+            sh.spins[r] = configs[(b0 + (c < cnt ? c : 0)) * N + (r - c * N)];
         }
         __syncthreads();
-        if (!tc_group_forward<C>(pl, sh, packed, st, err)) break;
-        for (int g = threadIdx.x; g < gc; g += blockDim.x) {
-            out[2 * (b0 + g)] = sh.a[g];
-            out[2 * (b0 + g) + 1] = sh.phi[g];
+        if (!tc_forward<C>(pl, sh, packed, st, err)) break;
+        for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+            const int s = c / G, g = c - s * G;
+            out[2 * (b0 + c)] = sh.res[s * 2 * G + g];
+            out[2 * (b0 + c) + 1] = sh.res[s * 2 * G + G + g];
         }
         __syncthreads();
     }
@@ -421,7 +458,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Probl
     TcShared sh;
     TcState st;
     tc_setup(pl, sh, smem, packed, st);
-    const int G = pl.G, N = pl.N;
+    const int G = pl.G, N = pl.N, per = G * pl.slots;
     unsigned char *ex = smem + pl.o_extra;
     int8_t *sigma = reinterpret_cast<int8_t *>(ex);
     int16_t *ci = reinterpret_cast<int16_t *>(ex + al16(N));
@@ -442,13 +479,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Probl
         __syncthreads();
         const int n_entries = nconn + recompute;
         bool ok = true;
-        for (int e0 = 0; e0 < n_entries; e0 += G) {
-            const int gc = min(G, n_entries - e0);
-            for (int r = threadIdx.x; r < G * N; r += blockDim.x) {
-                const int g = r / N, site = r - g * N;
-                const int k = e0 + g - recompute;
+        for (int e0 = 0; e0 < n_entries; e0 += per) {
+            const int cnt = min(per, n_entries - e0);
+            for (int r = threadIdx.x; r < per * N; r += blockDim.x) {
+                const int c = r / N, site = r - c * N;
+                const int k = e0 + c - recompute;
                 int v = sigma[site];
-                if (g < gc && k >= 0) {
+                if (c < cnt && k >= 0) {
                     const int i = ci[k], j = cj[k];
                     if (site == i) v = sigma[j];
                     else if (site == j) v = sigma[i];
@@ -456,10 +493,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Probl
                 sh.spins[r] = (int8_t)v;
             }
             __syncthreads();
-            if (!tc_group_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
-            if (threadIdx.x < gc) {
-                lp[2 * (e0 + threadIdx.x)] = sh.a[threadIdx.x];
-                lp[2 * (e0 + threadIdx.x) + 1] = sh.phi[threadIdx.x];
+            if (!tc_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
+            if (threadIdx.x < cnt) {
+                const int c = threadIdx.x, sl = c / G, g = c - sl * G;
+                lp[2 * (e0 + c)] = sh.res[sl * 2 * G + g];
+                lp[2 * (e0 + c) + 1] = sh.res[sl * 2 * G + G + g];
             }
         }
         if (!ok) break;
@@ -496,7 +534,8 @@ __device__ __forceinline__ int neighbour_dir_tc(int i, int d, int L) {
     return ((y + dy + L) % L) * L + (x + dx + L) % L;
 }
 
-// Metropolis exchange sampler; each block owns up to G chains.
+// Metropolis exchange sampler. Each block owns up to slots * G chains;
+// slot s evaluates the proposals of chains s * G ... s * G + G - 1.
 template <int C>
 __global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, const unsigned char *packed,
                                                                    int8_t *chains, int n_chains, int per_block,
@@ -507,70 +546,83 @@ __global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, con
     TcShared sh;
     TcState st;
     tc_setup(pl, sh, smem, packed, st);
-    const int G = pl.G, N = pl.N;
+    const int G = pl.G, N = pl.N, S = pl.slots;
     unsigned char *ex = smem + pl.o_extra;
     int8_t *cur = reinterpret_cast<int8_t *>(ex);                                // [per_block][N]
-    int *pi = reinterpret_cast<int *>(ex + al16(G * N));
-    int *pj = pi + G;
-    int *list = pj + G;                                                          // [G + 1]
-    double *pu = reinterpret_cast<double *>(ex + al16(G * N) + al16(4 * (3 * G + 1)));
-    double *ca = pu + G;
-    double *cphi = ca + G;
+    int *pi = reinterpret_cast<int *>(ex + al16(per_block * N));
+    int *pj = pi + per_block;
+    int *list = pj + per_block;                                                  // [S][G + 1]
+    double *pu = reinterpret_cast<double *>(ex + al16(per_block * N) + al16(4 * (2 * per_block + S * (G + 1))));
+    double *ca = pu + per_block;
+    double *cphi = ca + per_block;
     const int c0 = blockIdx.x * per_block;
     const int gc = min(per_block, n_chains - c0);
     bool ok = gc > 0;
     if (ok) {
         for (int r = threadIdx.x; r < gc * N; r += blockDim.x) cur[r] = chains[(size_t)c0 * N + r];
         __syncthreads();
-        for (int r = threadIdx.x; r < G * N; r += blockDim.x) {
-            const int g = r / N;
-            sh.spins[r] = cur[(g < gc ? g : 0) * N + (r - g * N)];
+        for (int r = threadIdx.x; r < per_block * N; r += blockDim.x) {
+            const int c = r / N;
+            sh.spins[r] = cur[(c < gc ? c : 0) * N + (r - c * N)];
         }
         __syncthreads();
-        ok = tc_group_forward<C>(pl, sh, packed, st, err);
-        for (int g = threadIdx.x; g < gc; g += blockDim.x) { ca[g] = sh.a[g]; cphi[g] = sh.phi[g]; }
+        ok = tc_forward<C>(pl, sh, packed, st, err);
+        for (int c = threadIdx.x; c < gc; c += blockDim.x) {
+            const int s = c / G, g = c - s * G;
+            ca[c] = sh.res[s * 2 * G + g];
+            cphi[c] = sh.res[s * 2 * G + G + g];
+        }
         __syncthreads();
     }
     const int n_sweeps = burn_in + spc * sweeps_between;
     for (int sweep = 0; ok && sweep < n_sweeps; ++sweep) {
         for (int q = 0; q < N; ++q) {
             const uint64_t step = step0 + (uint64_t)sweep * N + q;
-            for (int g = threadIdx.x; g < gc; g += blockDim.x) {
-                const Philox4 b = philox((uint64_t)(c0 + g), step, 0, 0, seed, 0);
+            for (int c = threadIdx.x; c < gc; c += blockDim.x) {
+                const Philox4 b = philox((uint64_t)(c0 + c), step, 0, 0, seed, 0);
                 const int i = (int)mulhi64(b.v[0], (uint64_t)N);
-                pi[g] = i;
-                pj[g] = neighbour_dir_tc(i, (int)(b.v[1] >> 62), pl.L);
-                pu[g] = (double)(b.v[2] >> 11) * 0x1.0p-53;
+                pi[c] = i;
+                pj[c] = neighbour_dir_tc(i, (int)(b.v[1] >> 62), pl.L);
+                pu[c] = (double)(b.v[2] >> 11) * 0x1.0p-53;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < S) {   // per-slot list of chains whose proposal changes the state
+                const int s = threadIdx.x;
                 int cnt = 0;
-                for (int g = 0; g < gc; ++g)
-                    if (cur[g * N + pi[g]] != cur[g * N + pj[g]]) list[cnt++] = g;
-                list[G] = cnt;
+                for (int g = 0; g < G; ++g) {
+                    const int c = s * G + g;
+                    if (c < gc && cur[c * N + pi[c]] != cur[c * N + pj[c]]) list[s * (G + 1) + cnt++] = c;
+                }
+                list[s * (G + 1) + G] = cnt;
             }
             __syncthreads();
-            const int cnt = list[G];
-            if (cnt == 0) continue;
-            for (int r = threadIdx.x; r < G * N; r += blockDim.x) {
-                const int m = r / N, site = r - m * N;
-                const int g = list[m < cnt ? m : 0];
-                const int i = pi[g], j = pj[g];
+            int total = 0;
+            for (int s = 0; s < S; ++s) total += list[s * (G + 1) + G];
+            if (total == 0) continue;
+            for (int r = threadIdx.x; r < per_block * N; r += blockDim.x) {
+                const int slot_row = r / N, site = r - slot_row * N;
+                const int s = slot_row / G, m = slot_row - s * G;
+                const int cnt = list[s * (G + 1) + G];
+                const int c = cnt > 0 ? list[s * (G + 1) + (m < cnt ? m : 0)] : 0;
+                const int i = cnt > 0 ? pi[c] : -1, j = cnt > 0 ? pj[c] : -1;
                 const int src = site == i ? j : (site == j ? i : site);
-                sh.spins[r] = cur[g * N + src];
+                sh.spins[r] = cur[c * N + src];
             }
             __syncthreads();
-            if (!tc_group_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
-            for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
-                const int g = list[m];
-                const double delta = 2.0 * (sh.a[m] - ca[g]);
-                if (delta >= 0.0 || pu[g] < exp(delta)) {
-                    const int i = pi[g], j = pj[g];
-                    const int8_t t = cur[g * N + i];
-                    cur[g * N + i] = cur[g * N + j];
-                    cur[g * N + j] = t;
-                    ca[g] = sh.a[m];
-                    cphi[g] = sh.phi[m];
+            if (!tc_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
+            for (int r = threadIdx.x; r < per_block; r += blockDim.x) {
+                const int s = r / G, m = r - s * G;
+                if (m >= list[s * (G + 1) + G]) continue;
+                const int c = list[s * (G + 1) + m];
+                const double an = sh.res[s * 2 * G + m];
+                const double delta = 2.0 * (an - ca[c]);
+                if (delta >= 0.0 || pu[c] < exp(delta)) {
+                    const int i = pi[c], j = pj[c];
+                    const int8_t t = cur[c * N + i];
+                    cur[c * N + i] = cur[c * N + j];
+                    cur[c * N + j] = t;
+                    ca[c] = an;
+                    cphi[c] = sh.res[s * 2 * G + G + m];
                 }
             }
             __syncthreads();
@@ -578,13 +630,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, con
         if (ok && sweep >= burn_in && (sweep - burn_in + 1) % sweeps_between == 0) {
             const int k = (sweep - burn_in + 1) / sweeps_between - 1;
             for (int r = threadIdx.x; r < gc * N; r += blockDim.x) {
-                const int g = r / N, site = r - g * N;
-                out_cfg[((size_t)(c0 + g) * spc + k) * N + site] = cur[r];
+                const int c = r / N, site = r - c * N;
+                out_cfg[((size_t)(c0 + c) * spc + k) * N + site] = cur[r];
             }
-            for (int g = threadIdx.x; g < gc; g += blockDim.x) {
-                out_logpsi[2 * ((size_t)(c0 + g) * spc + k)] = ca[g];
-                out_logpsi[2 * ((size_t)(c0 + g) * spc + k) + 1] = cphi[g];
-                if (!isfinite(ca[g])) atomicOr(err, ERRBIT_NONFINITE);
+            for (int c = threadIdx.x; c < gc; c += blockDim.x) {
+                out_logpsi[2 * ((size_t)(c0 + c) * spc + k)] = ca[c];
+                out_logpsi[2 * ((size_t)(c0 + c) * spc + k) + 1] = cphi[c];
+                if (!isfinite(ca[c])) atomicOr(err, ERRBIT_NONFINITE);
             }
             __syncthreads();
         }
@@ -595,33 +647,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, con
 }
 
 // ---------------------------------------------------------------- packing
-// fp32 block: w0s[o][ci][c] = W0[c][ci][o], biases[l][c], head[2][c];
-// bf16 block per layer l >= 1: B operand [o][kc][n][8]: element (o, k = c_in, n = c_out).
+// fp32 block: biases[l][c], head[2][c]. bf16 block of layer 0: B operand
+// [K0 / 8][C][8] with k = tap (J1-J2) or 3 tap + one-hot channel (t-J),
+// zero for k >= 9 c_in. bf16 block per layer l >= 1: [9][C / 8][C][8],
+// element (tap o, k = c_in, n = c_out).
 __global__ void tc_pack_kernel(Problem p, TcPlan pl, const double *params, unsigned char *packed) {
     const int C = p.C;
     float *f = reinterpret_cast<float *>(packed);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    for (int e = tid; e < 9 * p.c_in * C; e += nth) {
-        const int o = e / (p.c_in * C), rem = e - o * p.c_in * C, ci = rem / C, c = rem - ci * C;
-        f[e] = (float)params[(c * p.c_in + ci) * 9 + o];
-    }
     for (int e = tid; e < p.n_layers * C; e += nth) {
         const int l = e / C, c = e - l * C;
-        f[9 * p.c_in * C + e] = (float)params[layer_offset(p, l) + 9 * layer_cin(p, l) * C + c];
+        f[e] = (float)params[layer_offset(p, l) + 9 * layer_cin(p, l) * C + c];
     }
-    for (int e = tid; e < 2 * C; e += nth) f[9 * p.c_in * C + p.n_layers * C + e] = (float)params[head_offset(p) + e];
+    for (int e = tid; e < 2 * C; e += nth) f[p.n_layers * C + e] = (float)params[head_offset(p) + e];
+    __nv_bfloat16 *w0 = reinterpret_cast<__nv_bfloat16 *>(packed + pl.f32_bytes);
+    for (int e = tid; e < pl.K0 * C; e += nth) {
+        const int n = e / pl.K0, k = e - n * pl.K0;
+        float w = 0.f;
+        if (k < 9 * p.c_in) {
+            const int o = p.c_in == 1 ? k : k / 3, ci = p.c_in == 1 ? 0 : k % 3;
+            w = (float)params[(n * p.c_in + ci) * 9 + o];
+        }
+        w0[((k / 8) * C + n) * 8 + (k % 8)] = __float2bfloat16_rn(w);
+    }
     const int per = 9 * C * C;
     for (int e = tid; e < (p.n_layers - 1) * per; e += nth) {
         const int l = 1 + e / per, r = e - (l - 1) * per;
         const int o = r / (C * C), r2 = r - o * C * C, n = r2 / C, k = r2 - n * C;
         const double w = params[layer_offset(p, l) + (n * C + k) * 9 + o];
-        __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>(packed + pl.f32_bytes + (size_t)(l - 1) * pl.wbytes);
+        __nv_bfloat16 *dst =
+            reinterpret_cast<__nv_bfloat16 *>(packed + pl.f32_bytes + pl.w0bytes + (size_t)(l - 1) * pl.wbytes);
         dst[((o * (C / 8) + k / 8) * C + n) * 8 + (k % 8)] = __float2bfloat16_rn((float)w);
     }
 }
 
 // ---------------------------------------------------------------- host planning
-bool make_plan(const Problem &p, int G, size_t max_smem, int extra_bytes, TcPlan *out, std::string *why) {
+void plan_weights(const Problem &p, TcPlan &pl) {
+    pl.K0 = p.c_in == 1 ? 16 : 32;
+    pl.f32_count = p.n_layers * p.C + 2 * p.C;
+    pl.f32_bytes = al16(pl.f32_count * 4);
+    pl.w0bytes = (uint32_t)pl.K0 * p.C * 2u;
+    pl.wbytes = 9u * p.C * p.C * 2u;
+}
+
+bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_bytes, TcPlan *out, std::string *why) {
     TcPlan pl{};
     pl.L = p.L;
     pl.Lp = p.L + 2;
@@ -631,7 +700,8 @@ bool make_plan(const Problem &p, int G, size_t max_smem, int extra_bytes, TcPlan
     pl.KC = p.C / 8;
     pl.c_in = p.c_in;
     pl.n_layers = p.n_layers;
-    pl.n_tc = p.n_layers - 1;
+    pl.slots = slots;
+    plan_weights(p, pl);
     pl.count_out = (p.L - 1) * pl.Lp + p.L;
     pl.r0 = (pl.Lp + 1) * G;
     pl.n_tiles = (pl.count_out * G + 127) / 128;
@@ -639,58 +709,81 @@ bool make_plan(const Problem &p, int G, size_t max_smem, int extra_bytes, TcPlan
     pl.rbuf = std::max(pl.r0 + pl.n_tiles * 128 + reach, pl.Lp * pl.Lp * G);
     pl.rbuf = (pl.rbuf + 7) & ~7;
     pl.plane = (uint32_t)pl.rbuf * 16u;
-    pl.act_bytes = pl.plane * pl.KC;
-    pl.wbytes = 9u * p.C * p.C * 2u;
+    pl.act_bytes = pl.plane * (uint32_t)std::max(pl.KC, pl.K0 / 8);
+    pl.slot_cols = (uint32_t)(pl.n_tiles * p.C);
     uint32_t cols = 32;
-    while (cols < (uint32_t)(pl.n_tiles * p.C)) cols <<= 1;
+    while (cols < (uint32_t)slots * pl.slot_cols) cols <<= 1;
     pl.tmem_cols = cols;
-    pl.f32_count = 9 * p.c_in * p.C + p.n_layers * p.C + 2 * p.C;
-    pl.f32_bytes = al16(pl.f32_count * 4);
     uint32_t o = 0;
-    pl.o_act0 = o; o = al16(o + pl.act_bytes);
-    pl.o_act1 = o; o = al16(o + pl.act_bytes);
+    pl.o_act = o; o = al16(o + (uint32_t)slots * 2u * pl.act_bytes);
     pl.o_w0 = o; o = al16(o + pl.wbytes);
     pl.o_w1 = o; o = al16(o + pl.wbytes);
     pl.o_f32 = o; o = al16(o + pl.f32_count * 4);
     pl.o_rowtab = o; o = al16(o + 8 * pl.n_tiles * 128);
     pl.o_sitetab = o; o = al16(o + 8 * p.N);
-    pl.o_spad = o; o = al16(o + pl.Lp * pl.Lp * G);
-    pl.o_spins = o; o = al16(o + G * p.N);
-    pl.o_res = o; o = al16(o + 16 * G);
-    pl.o_bar = o; o = al16(o + 8 * (2 + kMaxTiles) + 8);
+    pl.o_spad = o; o = al16(o + slots * pl.Lp * pl.Lp * G);
+    pl.o_spins = o; o = al16(o + slots * G * p.N);
+    pl.o_res = o; o = al16(o + 16 * slots * G);
+    pl.o_bar = o; o = al16(o + 8 * (2 + kMaxSlots * kMaxTiles) + 8);
     pl.o_extra = o; o = al16(o + extra_bytes);
     // co-resident blocks must not ask for more than the SM's 512 TMEM
     // columns together: pad shared memory to cap residency
     const uint32_t sm_bytes = 233472u;   // 228 KB per SM, 1 KB reserved per block
     while (cols * (sm_bytes / (o + 1024u)) > 512u) o += 1024u;
     pl.total = o;
-    if (cols > 512) { *why = "tensor-memory tile does not fit in 512 columns"; return false; }
+    if (cols > 512) { *why = "tensor-memory tiles do not fit in 512 columns"; return false; }
     if (pl.n_tiles > kMaxTiles) { *why = "more than 16 row tiles per group"; return false; }
     if (pl.rbuf >= (int)kNone) { *why = "row index range exceeds 16 bits"; return false; }
     if (pl.total > max_smem) { *why = "shared memory plan exceeds the per-block limit"; return false; }
-    if (pl.n_tc < 1) { *why = "the tensor-core path needs at least two conv layers"; return false; }
     *out = pl;
     return true;
 }
 
-int eloc_extra(const Problem &p, int G) {
-    (void)G;
+int eloc_extra(const Problem &p) {
     return (int)(al16(p.N) + al16(4 * p.n_bonds) + al16(8 * p.n_bonds) + al16(4 * (p.N + 1)) + sizeof(EnumScratch) +
                  4 * sizeof(double) + 16 * (p.n_bonds + 1));
 }
 
-int sample_extra(const Problem &p, int G) { return (int)(al16(G * p.N) + al16(4 * (3 * G + 1)) + 24 * G); }
+int sample_extra(const Problem &p, int G, int slots) {
+    const int per = G * slots;
+    return (int)(al16(per * p.N) + al16(4 * (2 * per + slots * (G + 1))) + 24 * per);
+}
 
-// Choose G maximising useful rows / computed rows within the limits.
+// Relative throughput of a one-slot plan: useful rows per computed row,
+// with a fixed cost of four tiles per forward (inputs, head, barriers).
+double plan_score(const Problem &p, const TcPlan &pl) {
+    return (double)(p.N * pl.G) / (double)(pl.n_tiles * 128 + 4 * 128);
+}
+
+// NQS_TC_PLAN="G,slots" forces a plan (tuning); ignored if infeasible.
+bool forced_plan(int *G, int *slots) {
+    const char *s = getenv("NQS_TC_PLAN");
+    return s && sscanf(s, "%d,%d", G, slots) == 2 && *G >= 1 && *G <= 16 && *slots >= 1 && *slots <= kMaxSlots;
+}
+
 bool best_plan(const Problem &p, size_t max_smem, bool eloc, int gmax, TcPlan *out, std::string *why) {
+    int fg, fs;
+    if (forced_plan(&fg, &fs) && make_plan(p, fg, fs, max_smem, eloc ? eloc_extra(p) : 0, out, why)) return true;
+    // best one-slot plan; then two slots of the same G when they fit and a
+    // slot has few tiles (measured on GB300: the epilogue tail after the last
+    // MMA of a layer is then a large share of the layer, and the second slot
+    // hides it; with many tiles the extra shared memory costs more than it saves)
     double best = -1.0;
     bool found = false;
     for (int G = 1; G <= gmax; ++G) {
         TcPlan pl;
         std::string w;
-        if (!make_plan(p, G, max_smem, eloc ? eloc_extra(p, G) : 0, &pl, &w)) { if (!found) *why = w; continue; }
-        const double eff = (double)(p.N * G) / (double)(pl.n_tiles * 128);
-        if (eff > best + 1e-9) { best = eff; *out = pl; found = true; }
+        if (!make_plan(p, G, 1, max_smem, eloc ? eloc_extra(p) : 0, &pl, &w)) {
+            if (!found) *why = w;
+            continue;
+        }
+        const double sc = plan_score(p, pl);
+        if (sc > best + 1e-9) { best = sc; *out = pl; found = true; }
+    }
+    if (found && out->n_tiles <= 8) {
+        TcPlan two;
+        std::string w;
+        if (make_plan(p, out->G, 2, max_smem, eloc ? eloc_extra(p) : 0, &two, &w)) *out = two;
     }
     return found;
 }
@@ -715,31 +808,24 @@ int prep(K kernel, const TcPlan &pl, const LaunchEnv &env) {
     return NQS_OK;
 }
 
-TcPlan plan_for_pack(const Problem &p) {
-    TcPlan pl{};
-    pl.f32_count = 9 * p.c_in * p.C + p.n_layers * p.C + 2 * p.C;
-    pl.f32_bytes = al16(pl.f32_count * 4);
-    pl.wbytes = 9u * p.C * p.C * 2u;
-    return pl;
-}
-
 }  // namespace
 
 bool tc_supported(const Problem &p, std::string *why) {
     if (p.C != 16 && p.C != 32) { *why = "the tensor-core path needs 16 or 32 channels"; return false; }
-    if (p.n_layers < 2) { *why = "the tensor-core path needs at least two conv layers"; return false; }
     return true;
 }
 
 size_t tc_packed_bytes(const Problem &p) {
-    const TcPlan pl = plan_for_pack(p);
-    return pl.f32_bytes + (size_t)(p.n_layers > 1 ? p.n_layers - 1 : 0) * pl.wbytes;
+    TcPlan pl{};
+    plan_weights(p, pl);
+    return pl.f32_bytes + pl.w0bytes + (size_t)(p.n_layers - 1) * pl.wbytes;
 }
 
 int launch_tc_pack(const Problem &p, const double *p64, void *packed, const LaunchEnv &env) {
     std::string why;
     if (!tc_supported(p, &why)) { *env.msg = why; return NQS_ERR_UNSUPPORTED; }
-    const TcPlan pl = plan_for_pack(p);
+    TcPlan pl{};
+    plan_weights(p, pl);
     tc_pack_kernel<<<64, 256, 0, env.stream>>>(p, pl, p64, (unsigned char *)packed);
     return check(env, "tc_pack_kernel");
 }
@@ -757,8 +843,8 @@ int launch_logpsi_tc(const Problem &p, const double *, const void *packed, const
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
-    const int64_t groups = (n + pl.G - 1) / pl.G;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, env.num_sms));
+    const int64_t per = pl.G * pl.slots;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, env.num_sms));
     NQS_TC_DISPATCH(p.C, {
         auto k = logpsi_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
@@ -791,14 +877,16 @@ int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_
                      double *out_logpsi, const LaunchEnv &env) {
     std::string why;
     if (!tc_supported(p, &why)) { *env.msg = why; return NQS_ERR_UNSUPPORTED; }
-    // chains per block: enough blocks to cover the SMs, at most G
+    // chains per block: enough blocks to cover the SMs; two slots when a
+    // block owns at least two chains
     const int want = std::max(1, (n_chains + env.num_sms - 1) / env.num_sms);
+    const int slots = want >= 2 ? 2 : 1;
     TcPlan pl;
     bool ok = false;
-    for (int G = std::min(want, 16); G >= 1 && !ok; --G)
-        ok = make_plan(p, G, env.max_smem, sample_extra(p, G), &pl, &why);
+    for (int G = std::min((want + slots - 1) / slots, 16); G >= 1 && !ok; --G)
+        ok = make_plan(p, G, slots, env.max_smem, sample_extra(p, G, slots), &pl, &why);
     if (!ok) { *env.msg = why; return NQS_ERR_UNSUPPORTED; }
-    const int per_block = pl.G;
+    const int per_block = pl.G * pl.slots;
     const int grid = (n_chains + per_block - 1) / per_block;
     NQS_TC_DISPATCH(p.C, {
         auto k = sample_tc_kernel<CC>;
