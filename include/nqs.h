@@ -170,6 +170,33 @@ int nqs_set_chains(nqs_ctx *ctx, int32_t n_chains, const int8_t *chains, uint64_
  * O_k = row s + i * row (n + s). */
 int nqs_logpsi_grad(nqs_ctx *ctx, const int8_t *configs, int64_t n, double *O_out, int32_t precision);
 
+/* Local derivatives without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (code that runs where allocating is not allowed, such as an
+ * application that owns all device memory through its own allocator, or a
+ * framework that forbids allocations from libraries while it records work),
+ * and that therefore cannot create an nqs_ctx either.
+ * It computes exactly what nqs_logpsi_grad computes (same kernel; output
+ * O_out device float64 [2n][P], real-stacked as there), for the problem p,
+ * the device float64 parameters `params` and the device int8 configurations
+ * [n][N], enqueued on `stream` (cudaStream_t, NULL = legacy default stream)
+ * of the current device.
+ * Working memory: one fixed device array of 8 MiB that the library defines
+ * at file scope (every GPU that loads the library holds it until the
+ * process exits). The call rejects, with NQS_ERR_UNSUPPORTED, problems
+ * whose per-block working arrays (plus a float32 copy of the parameters
+ * for NQS_FP32 / NQS_BF16) do not fit in it. All calls share the array and
+ * it keeps the last call's contents; calls that overlap on the same GPU
+ * (issued on two streams, or from two host threads) race on it, so the
+ * caller must serialise them. Each GPU has its own copy of the array.
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Returns NQS_OK or a negative nqs_status; nqs_noalloc_last_error gives a
+ * one-line description of the last failure of the calling host thread. */
+int nqs_logpsi_grad_noalloc(const nqs_problem *p, const double *params, const int8_t *configs, int64_t n,
+                            double *O_out, int32_t precision, void *stream);
+const char *nqs_noalloc_last_error(void);
+
 /* Stochastic reconfiguration (Sec. 3.2; Sec. 5.4.1 "Distributed SR
  * computation", solved here matrix-free by conjugate gradient):
  *   <E> = mean E_loc, Oc = O - mean O,

@@ -591,3 +591,113 @@ int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const 
 }
 
 }  // namespace nqs
+
+// ------------------------------------------------------------------ allocation-free local derivatives
+// Some callers cannot allocate device memory: code running where cudaMalloc
+// is not allowed (inside a stream capture of a larger graph, under an
+// allocator that forbids foreign allocations, or in a process that manages
+// all device memory itself). nqs_logpsi_grad_noalloc serves them: it runs
+// the same per-sample backward kernel, with its per-block working arrays in
+// a fixed device array that the library defines at file scope, so the call
+// itself allocates nothing. Every GPU that loads the library holds this
+// array until the process exits. All calls share it and it keeps the last
+// call's contents; calls whose work overlaps on the GPU (two streams, two
+// host threads) race on it and must be serialised by the caller.
+#include <mutex>
+
+namespace nqs {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 8u << 20;   // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNoAllocMaxDevices];     // device address of the array, per device
+thread_local std::string g_noalloc_error;
+
+}  // namespace
+
+}  // namespace nqs
+
+extern "C" int64_t nqs_param_count(const nqs_problem *p);
+
+extern "C" const char *nqs_noalloc_last_error(void) { return nqs::g_noalloc_error.c_str(); }
+
+extern "C" int nqs_logpsi_grad_noalloc(const nqs_problem *q, const double *params, const int8_t *configs, int64_t n,
+                                       double *O_out, int32_t precision, void *stream) {
+    using namespace nqs;
+    const int64_t P = nqs_param_count(q);
+    if (P < 0) { g_noalloc_error = "invalid problem"; return NQS_ERR_INVALID_ARG; }
+    if (precision != NQS_FP64 && precision != NQS_FP32 && precision != NQS_BF16) {
+        g_noalloc_error = "bad precision";
+        return NQS_ERR_INVALID_ARG;
+    }
+    if (n < 0 || (n > 0 && (!params || !configs || !O_out))) { g_noalloc_error = "bad arrays"; return NQS_ERR_INVALID_ARG; }
+    if (n == 0) return NQS_OK;
+    Problem p;
+    p.model = q->model;
+    p.L = q->L;
+    p.N = q->L * q->L;
+    p.c_in = q->model == NQS_MODEL_J1J2 ? 1 : 3;
+    p.C = q->channels;
+    p.n_layers = q->n_layers;
+    p.J1 = q->J1; p.J2 = q->J2; p.t = q->t; p.J = q->J;
+    p.sign_rule = q->sign_rule;
+    p.P = (int)P;
+    p.n_bonds = (q->model == NQS_MODEL_J1J2 ? 4 : 2) * p.N;
+    p.n_up = q->n_up;
+    p.n_down = q->n_down;
+    // the bf16 precision differentiates with float32 internals, as nqs_logpsi_grad does
+    const bool f64 = precision == NQS_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    const size_t params_bytes = f64 ? 0 : align16((size_t)P * 4);
+    const size_t per_block = grad_per_block(p) * esz;
+    if (params_bytes + per_block > kNoAllocScratchBytes) {
+        g_noalloc_error = "problem needs " + std::to_string(params_bytes + per_block) +
+                           " bytes of working memory; the fixed array holds " + std::to_string(kNoAllocScratchBytes);
+        return NQS_ERR_UNSUPPORTED;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    void *base = nullptr;
+    {
+        // first call on this device: resolve the array's device address (the
+        // host-side symbol is only a stand-in); do this before any capture
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                g_noalloc_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+                return NQS_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = ptr;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    int num_sms = 0;
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { g_noalloc_error = cudaGetErrorString(e); return NQS_ERR_CUDA; }
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int64_t fit = (int64_t)((kNoAllocScratchBytes - params_bytes) / per_block);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n, fit), (int64_t)num_sms * 2));
+    unsigned char *scratch = static_cast<unsigned char *>(base) + params_bytes;
+    if (f64) {
+        grad_plain_kernel<double><<<blocks, kThreads, 0, s>>>(p, params, params, configs, n, O_out,
+                                                               reinterpret_cast<double *>(scratch), grad_per_block(p));
+    } else {
+        float *p32 = static_cast<float *>(base);
+        convert_params_kernel<<<(p.P + 255) / 256, 256, 0, s>>>(params, p32, p.P);
+        grad_plain_kernel<float><<<blocks, kThreads, 0, s>>>(p, p32, params, configs, n, O_out,
+                                                              reinterpret_cast<float *>(scratch), grad_per_block(p));
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { g_noalloc_error = std::string("launch: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
+    return NQS_OK;
+}

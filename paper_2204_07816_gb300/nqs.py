@@ -25,7 +25,7 @@ MODEL = {'j1j2': 0, 'tj': 1}
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
-           'nqs_logpsi_grad', 'nqs_sr_solve')
+           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve')
 
 
 class nqs_problem(ctypes.Structure):
@@ -67,6 +67,8 @@ def load(path=LIB_PATH):
         'nqs_get_chains': (ctypes.c_int, [P, I32, P, ctypes.POINTER(U64)]),
         'nqs_set_chains': (ctypes.c_int, [P, I32, P, U64]),
         'nqs_logpsi_grad': (ctypes.c_int, [P, P, I64, P, I32]),
+        'nqs_logpsi_grad_noalloc': (ctypes.c_int, [ctypes.POINTER(nqs_problem), P, P, I64, P, I32, P]),
+        'nqs_noalloc_last_error': (ctypes.c_char_p, []),
         'nqs_sr_solve': (ctypes.c_int, [P, P, P, I64, D, D, I32, D, P, ctypes.POINTER(I32), ctypes.POINTER(D),
                                         ctypes.POINTER(D), I32]),
     }
@@ -107,6 +109,21 @@ def make_problem(model='j1j2', L=4, J1=1.0, J2=0.5, t=1.0, J=0.4, n_up=None, n_d
 
 def nqs_param_count(problem):
     return load().nqs_param_count(ctypes.byref(problem))
+
+
+def nqs_logpsi_grad_noalloc(problem, params, configs, O_out, precision='fp64', stream=None):
+    """Local derivatives through the allocation-free entry point (no context,
+    no device allocation; see include/nqs.h). O_out: float64 [2n, P]."""
+    lib = load()
+    n = configs.shape[0]
+    if stream is None:
+        stream = torch.cuda.current_stream(configs.device)
+    rc = lib.nqs_logpsi_grad_noalloc(ctypes.byref(problem), _ptr(params, torch.float64, 'params'),
+                                     _ptr(configs, torch.int8, 'configs'), n, _ptr(O_out, torch.float64, 'O_out'),
+                                     _prec(precision), ctypes.c_void_p(stream.cuda_stream))
+    if rc != NQS_OK:
+        raise NQSError(rc, lib.nqs_noalloc_last_error().decode())
+    return O_out
 
 
 class Context:
