@@ -877,10 +877,11 @@ int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_
                      double *out_logpsi, const LaunchEnv &env) {
     std::string why;
     if (!tc_supported(p, &why)) { *env.msg = why; return NQS_ERR_UNSUPPORTED; }
-    // chains per block: enough blocks to cover the SMs; two slots when a
-    // block owns at least two chains
+    // chains per block: enough blocks to cover the SMs, one group in flight
+    // (measured: with one or two chains per block a second slot only adds
+    // fixed per-forward costs)
     const int want = std::max(1, (n_chains + env.num_sms - 1) / env.num_sms);
-    const int slots = want >= 2 ? 2 : 1;
+    const int slots = want >= 8 ? 2 : 1;
     TcPlan pl;
     bool ok = false;
     for (int G = std::min((want + slots - 1) / slots, 16); G >= 1 && !ok; --G)
