@@ -321,6 +321,12 @@ int nqs_logpsi_grad(nqs_ctx *c, const int8_t *configs, int64_t n, double *O, int
     const int gp = prec == NQS_FP64 ? NQS_FP64 : NQS_FP32;
     DeviceParams dp;
     if (int rc = prepare_params(c, gp, &dp)) return rc;
+    if (gp == NQS_FP32 && grad_fast_supported(c->p, c->max_smem)) {
+        const int fb = (int)std::min<int64_t>(n, (int64_t)c->num_sms * grad_fast_blocks_per_sm(c->p));
+        if (int rc = ensure_scratch(c, grad_fast_scratch_bytes(c->p, fb))) return rc;
+        LaunchEnv env = env_of(c);
+        return launch_grad_fast(c->p, c->params32, c->params, configs, n, O, c->scratch, c->scratch_bytes, env);
+    }
     const int blocks = (int)std::min<int64_t>(n, (int64_t)c->num_sms * 2);
     if (int rc = ensure_scratch(c, grad_scratch_bytes(c->p, gp, blocks))) return rc;
     LaunchEnv env = env_of(c);

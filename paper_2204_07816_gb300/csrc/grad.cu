@@ -1,0 +1,290 @@
+// Per-sample local derivatives O_k = d log W / d theta_k (Sec. 3.2: the
+// backward of the network gives O_loc) with float32 internals, for the
+// FP32 and tensor-core precisions. One block per sample at a time:
+//   forward   z_l = conv(h_{l-1}) + b_l, h_l = silu(z_l); h_l and
+//             s_l = sigmoid(z_l) go to this block's (L2-resident) scratch
+//   head      d a / d w_a = d phi / d w_phi = sum over sites of h_n
+//   backward  for l = n_l - 1 .. 0, both outputs (a and phi) at once:
+//             gz = g * silu'(z) with silu'(z) = s + h (1 - s)
+//             dW[o][c][k] = sum_site gz[o][site] h_{l-1}[c][site + d_k]
+//             db[o] = sum_site gz[o][site]
+//             g_{l-1}[c][site] = sum_{o,k} W[o][c][k] gz[o][site - d_k]
+// Every working array of the current layer lives in shared memory with a
+// site stride of N + 1 (odd) so that threads reading different channels hit
+// different banks; neighbour indices come from a table built once.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace nqs {
+
+namespace {
+
+constexpr int kGradThreads = 256;
+
+struct GradLayout {
+    int NP;                // padded site stride
+    size_t w, nbr, hprev, gz, gnext, hbar, total;
+};
+
+__host__ __device__ inline size_t a16(size_t v) { return (v + 15) & ~size_t(15); }
+
+__host__ __device__ inline GradLayout grad_layout(const Problem &p) {
+    GradLayout g;
+    g.NP = p.N + 1;
+    const int cmax = p.C > p.c_in ? p.C : p.c_in;
+    size_t o = 0;
+    g.w = o; o = a16(o + 4 * (size_t)(9 * p.C * cmax + p.C));
+    g.nbr = o; o = a16(o + 2 * (size_t)9 * p.N);
+    g.hprev = o; o = a16(o + 4 * (size_t)cmax * g.NP);
+    g.gz = o; o = a16(o + 4 * (size_t)2 * p.C * g.NP);
+    g.gnext = o; o = a16(o + 4 * (size_t)2 * p.C * g.NP);
+    g.hbar = o; o = a16(o + 4 * (size_t)p.C);
+    g.total = o;
+    return g;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kGradThreads) grad_fast_kernel(Problem p, const float *__restrict__ prm,
+                                                                const double *__restrict__ p64,
+                                                                const int8_t *__restrict__ configs, int64_t n,
+                                                                double *__restrict__ O, float *__restrict__ scratch,
+                                                                size_t per_block) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GradLayout gl = grad_layout(p);
+    const int N = p.N, NP = gl.NP, L = p.L, nl = p.n_layers, P = p.P;
+    float *w = reinterpret_cast<float *>(smem + gl.w);
+    int16_t *nbr = reinterpret_cast<int16_t *>(smem + gl.nbr);      // [9][N]: site at (x + dx, y + dy)
+    float *hprev = reinterpret_cast<float *>(smem + gl.hprev);      // [cin][NP]
+    float *gz = reinterpret_cast<float *>(smem + gl.gz);            // [2][C][NP] (forward: output h)
+    float *gnext = reinterpret_cast<float *>(smem + gl.gnext);      // [2][C][NP]
+    float *hbar = reinterpret_cast<float *>(smem + gl.hbar);
+    float *Hs = scratch + per_block * blockIdx.x;                    // [nl][C][N] h
+    float *Ss = Hs + (size_t)nl * C * N;                             // [nl][C][N] sigmoid(z)
+
+    for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+        const int k = e / N, s = e - k * N;
+        const int x = s % L, y = s / L, dy = k / 3 - 1, dx = k % 3 - 1;
+        nbr[e] = (int16_t)((((y + dy) % L + L) % L) * L + ((x + dx) % L + L) % L);
+    }
+    __syncthreads();
+
+    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x) {
+        double *Oa = O + (size_t)smp * P;
+        double *Op = O + (size_t)(n + smp) * P;
+        const int8_t *cfg = configs + smp * N;
+        // ---------------- forward
+        for (int s = threadIdx.x; s < N; s += blockDim.x) {
+            const int v = cfg[s];
+            if (p.c_in == 1) hprev[s] = (float)v;
+            else { hprev[s] = (float)(v == 0); hprev[NP + s] = (float)(v == 1); hprev[2 * NP + s] = (float)(v == -1); }
+        }
+        for (int l = 0; l < nl; ++l) {
+            const int cin = layer_cin(p, l), off = layer_offset(p, l);
+            __syncthreads();
+            // stage W as w[(k * cin + c) * C + o], bias after
+            for (int e = threadIdx.x; e < 9 * cin * C; e += blockDim.x) {
+                const int o = e / (9 * cin), rem = e - o * 9 * cin, c = rem / 9, k = rem - c * 9;
+                w[(k * cin + c) * C + o] = prm[off + e];
+            }
+            for (int e = threadIdx.x; e < C; e += blockDim.x) w[9 * cin * C + e] = prm[off + 9 * cin * C + e];
+            __syncthreads();
+            float *hout = gz;   // [C][NP]
+            for (int s = threadIdx.x; s < N; s += blockDim.x) {
+                float acc[C];
+#pragma unroll
+                for (int o = 0; o < C; ++o) acc[o] = w[9 * cin * C + o];
+                for (int k = 0; k < 9; ++k) {
+                    const int sn = nbr[k * N + s];
+                    for (int c = 0; c < cin; ++c) {
+                        const float hv = hprev[c * NP + sn];
+                        const float4 *wr = reinterpret_cast<const float4 *>(w + (k * cin + c) * C);
+#pragma unroll
+                        for (int q = 0; q < C / 4; ++q) {
+                            const float4 wv = wr[q];
+                            acc[4 * q] = fmaf(wv.x, hv, acc[4 * q]);
+                            acc[4 * q + 1] = fmaf(wv.y, hv, acc[4 * q + 1]);
+                            acc[4 * q + 2] = fmaf(wv.z, hv, acc[4 * q + 2]);
+                            acc[4 * q + 3] = fmaf(wv.w, hv, acc[4 * q + 3]);
+                        }
+                    }
+                }
+                float *Hl = Hs + (size_t)l * C * N, *Sl = Ss + (size_t)l * C * N;
+#pragma unroll
+                for (int o = 0; o < C; ++o) {
+                    const float sg = 1.0f / (1.0f + expf(-acc[o]));
+                    const float h = acc[o] * sg;
+                    hout[o * NP + s] = h;
+                    Hl[o * N + s] = h;
+                    Sl[o * N + s] = sg;
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
+                const int c = e / N, s = e - c * N;
+                hprev[c * NP + s] = hout[c * NP + s];
+            }
+        }
+        __syncthreads();
+        // ---------------- head
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int c = warp; c < C; c += nw) {
+                float v = 0.f;
+                for (int s = lane; s < N; s += 32) v += hprev[c * NP + s];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) hbar[c] = v;
+            }
+        }
+        __syncthreads();
+        const int ho = head_offset(p);
+        for (int c = threadIdx.x; c < C; c += blockDim.x) {
+            Oa[ho + c] = (double)hbar[c];
+            Oa[ho + C + c] = 0.0;
+            Op[ho + c] = 0.0;
+            Op[ho + C + c] = (double)hbar[c];
+        }
+        for (int e = threadIdx.x; e < 2 * C * N; e += blockDim.x) {
+            const int r = e / (C * N), rem = e - r * C * N, c = rem / N, s = rem - c * N;
+            gnext[(r * C + c) * NP + s] = (float)p64[ho + r * C + c];
+        }
+        // ---------------- backward
+        for (int l = nl - 1; l >= 0; --l) {
+            const int cin = layer_cin(p, l), off = layer_offset(p, l);
+            const float *Hl = Hs + (size_t)l * C * N, *Sl = Ss + (size_t)l * C * N;
+            __syncthreads();
+            for (int e = threadIdx.x; e < 2 * C * N; e += blockDim.x) {
+                const int r = e / (C * N), rem = e - r * C * N, c = rem / N, s = rem - c * N;
+                const float h = Hl[c * N + s], sg = Sl[c * N + s];
+                gz[(r * C + c) * NP + s] = gnext[(r * C + c) * NP + s] * (sg + h * (1.0f - sg));
+            }
+            // layer input h_{l-1} and the weights in [o][k][c] order (c contiguous)
+            if (l == 0) {
+                for (int s = threadIdx.x; s < N; s += blockDim.x) {
+                    const int v = cfg[s];
+                    if (p.c_in == 1) hprev[s] = (float)v;
+                    else { hprev[s] = (float)(v == 0); hprev[NP + s] = (float)(v == 1); hprev[2 * NP + s] = (float)(v == -1); }
+                }
+            } else {
+                const float *Hp = Hs + (size_t)(l - 1) * C * N;
+                for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
+                    const int c = e / N, s = e - c * N;
+                    hprev[c * NP + s] = Hp[e];
+                }
+            }
+            for (int e = threadIdx.x; e < 9 * cin * C; e += blockDim.x) {
+                const int o = e / (9 * cin), rem = e - o * 9 * cin, c = rem / 9, k = rem - c * 9;
+                w[(o * 9 + k) * cin + c] = prm[off + e];
+            }
+            __syncthreads();
+            // weight and bias gradients, both outputs
+            for (int pc = threadIdx.x; pc < C * cin; pc += blockDim.x) {
+                const int o = pc / cin, c = pc - o * cin;
+                float a0[9], a1[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) { a0[k] = 0.f; a1[k] = 0.f; }
+                const float *g0 = gz + o * NP, *g1 = gz + (C + o) * NP;
+                const float *hc = hprev + c * NP;
+                for (int s = 0; s < N; ++s) {
+                    const float x0 = g0[s], x1 = g1[s];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const float hv = hc[nbr[k * N + s]];
+                        a0[k] = fmaf(x0, hv, a0[k]);
+                        a1[k] = fmaf(x1, hv, a1[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    Oa[off + (o * cin + c) * 9 + k] = (double)a0[k];
+                    Op[off + (o * cin + c) * 9 + k] = (double)a1[k];
+                }
+            }
+            {
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                for (int ro = warp; ro < 2 * C; ro += nw) {
+                    float v = 0.f;
+                    for (int s = lane; s < N; s += 32) v += gz[ro * NP + s];
+#pragma unroll
+                    for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
+                    if (lane == 0) (ro < C ? Oa : Op)[off + 9 * cin * C + (ro % C)] = (double)v;
+                }
+            }
+            if (l > 0) {
+                // input gradient g_{l-1}[r][c][s] = sum_{o,k} W[o][c][k] gz[r][o][s - d_k]
+                for (int rs = threadIdx.x; rs < 2 * N; rs += blockDim.x) {
+                    const int r = rs / N, s = rs - r * N;
+                    float acc[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+                    const float *gr = gz + r * C * NP;
+                    for (int k = 0; k < 9; ++k) {
+                        const int sm = nbr[(8 - k) * N + s];   // site - d_k
+                        for (int o = 0; o < C; ++o) {
+                            const float gv = gr[o * NP + sm];
+                            const float4 *wr = reinterpret_cast<const float4 *>(w + (o * 9 + k) * C);
+#pragma unroll
+                            for (int q = 0; q < C / 4; ++q) {
+                                const float4 wv = wr[q];
+                                acc[4 * q] = fmaf(wv.x, gv, acc[4 * q]);
+                                acc[4 * q + 1] = fmaf(wv.y, gv, acc[4 * q + 1]);
+                                acc[4 * q + 2] = fmaf(wv.z, gv, acc[4 * q + 2]);
+                                acc[4 * q + 3] = fmaf(wv.w, gv, acc[4 * q + 3]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < C; ++c) gnext[(r * C + c) * NP + s] = acc[c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int grad_fast_blocks_per_sm(const Problem &p) {
+    const size_t smem = grad_layout(p).total + 1024;
+    return (int)std::max<size_t>(1, std::min<size_t>(4, 233472 / smem));
+}
+
+bool grad_fast_supported(const Problem &p, size_t max_smem) {
+    return (p.C == 16 || p.C == 32) && grad_layout(p).total <= max_smem;
+}
+
+size_t grad_fast_scratch_bytes(const Problem &p, int num_blocks) {
+    return (size_t)2 * p.n_layers * p.C * p.N * sizeof(float) * num_blocks;
+}
+
+int launch_grad_fast(const Problem &p, const float *p32, const double *p64, const int8_t *configs, int64_t n,
+                     double *O, void *scratch, size_t scratch_bytes, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    const GradLayout gl = grad_layout(p);
+    const size_t per_block = (size_t)2 * p.n_layers * p.C * p.N;   // floats
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(n, (int64_t)env.num_sms * grad_fast_blocks_per_sm(p)),
+                             (int64_t)(scratch_bytes / (per_block * sizeof(float)))));
+    cudaError_t e;
+    if (p.C == 16) {
+        e = cudaFuncSetAttribute(grad_fast_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gl.total);
+        if (e == cudaSuccess)
+            grad_fast_kernel<16><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, O,
+                                                                                 (float *)scratch, per_block);
+    } else {
+        e = cudaFuncSetAttribute(grad_fast_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gl.total);
+        if (e == cudaSuccess)
+            grad_fast_kernel<32><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, O,
+                                                                                 (float *)scratch, per_block);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *env.msg = std::string("grad_fast_kernel: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    ++*env.launches;
+    return NQS_OK;
+}
+
+}  // namespace nqs

@@ -42,6 +42,12 @@ int launch_sample_plain(const Problem &p, int prec, const DeviceParams &dp, int8
 int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
                       double *O, void *scratch, size_t scratch_bytes, const LaunchEnv &env);
 size_t grad_scratch_bytes(const Problem &p, int prec, int num_blocks);
+// float32-internal backward with shared-memory working sets (grad.cu)
+bool grad_fast_supported(const Problem &p, size_t max_smem);
+int grad_fast_blocks_per_sm(const Problem &p);
+size_t grad_fast_scratch_bytes(const Problem &p, int num_blocks);
+int launch_grad_fast(const Problem &p, const float *p32, const double *p64, const int8_t *configs, int64_t n,
+                     double *O, void *scratch, size_t scratch_bytes, const LaunchEnv &env);
 void launch_convert_params(const double *p64, float *p32, int P, cudaStream_t s);
 
 // ---- tensor-core path (tc.cu)

@@ -221,15 +221,19 @@ def test_logpsi_grad_fp64(case):
     assert rel_err(O[9:], dPhi) <= 1e-10
 
 
-def test_logpsi_grad_fp32():
-    w = WL['j1j2_10x10']
-    ctx, params = make_ctx(w)
-    spec, _ = oracle_of(w)
-    cfg = configs_for(w, 4, seed=13)
-    O = ctx.logpsi_grad(dev(cfg), 'fp32').cpu().numpy()
+@pytest.mark.parametrize('case', [('j1j2_10x10', {}), ('tj_12x12', {}), ('j1j2_16x16', {'n_layers': 3}),
+                                  ('j1j2_4x4', {'channels': 16, 'n_layers': 2})], ids=_ids)
+@pytest.mark.parametrize('prec', ['fp32', 'bf16'])
+def test_logpsi_grad_fp32_internals(case, prec):
+    name, over = case
+    w = WL[name]
+    ctx, params = make_ctx(w, **over)
+    spec, _ = oracle_of(w, **over)
+    cfg = configs_for(w, 5, seed=13, **over)
+    O = ctx.logpsi_grad(dev(cfg), prec).cpu().numpy()
     _, _, dA, dPhi = cnn.backward(params, cfg, spec)
-    assert rel_err(O[:4], dA) <= 1e-4
-    assert rel_err(O[4:], dPhi) <= 1e-4
+    assert rel_err(O[:5], dA) <= 1e-4
+    assert rel_err(O[5:], dPhi) <= 1e-4
 
 
 def test_sr_solve_matches_oracle():
