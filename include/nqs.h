@@ -141,6 +141,22 @@ int nqs_connected(nqs_ctx *ctx, const int8_t *configs, int64_t n, int32_t max_co
 int nqs_local_energy(nqs_ctx *ctx, const int8_t *configs, const double *logpsi, int64_t n,
                      double *eloc_out, int32_t precision);
 
+/* Local energies of several independent problems in one pass (the
+ * batched, fixed-length forward of Sec. 5.4.1 "Thread-level parallel
+ * MCMC", extended across problems of different lattice sizes and
+ * Hamiltonians). Entry i evaluates what nqs_local_energy(ctxs[i],
+ * configs[i], logpsi ? logpsi[i] : NULL, n[i], eloc_out[i], precision)
+ * evaluates, with bitwise the same results. With NQS_BF16 the problems that
+ * share a channel count run in one tensor-core launch whose blocks move from
+ * problem to problem; the CUDA-core precisions run one launch per problem.
+ * All work is enqueued on the stream of ctxs[0], which must be on the same
+ * device as the others; the caller orders it after the work that produces
+ * the inputs (e.g. with events). Host arrays of `count` entries; device
+ * arrays as in nqs_local_energy. */
+int nqs_local_energy_multi(nqs_ctx *const *ctxs, int32_t count, const int8_t *const *configs,
+                           const double *const *logpsi, const int64_t *n, double *const *eloc_out,
+                           int32_t precision);
+
 /* Metropolis exchange sampling from |W(S)|^2 (Sec. 3.2; Sec. 5.4.1
  * "Process-level / thread-level parallel MCMC": many independent chains).
  * The context keeps n_chains chains on the device across calls; the first

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -27,6 +28,8 @@ struct nqs_ctx {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int64_t launches = 0;
+    void *multi_table = nullptr;   // request table of grouped launches led by this context
+    size_t multi_table_bytes = 0;
     std::string msg;
 };
 
@@ -204,8 +207,75 @@ int nqs_destroy(nqs_ctx *c) {
     cudaFree(c->packed);
     cudaFree(c->chains);
     cudaFree(c->scratch);
+    cudaFree(c->multi_table);
     delete c;
     return rc;
+}
+
+int nqs_local_energy_multi(nqs_ctx *const *ctxs, int32_t count, const int8_t *const *configs,
+                           const double *const *logpsi, const int64_t *n, double *const *eloc_out, int32_t prec) {
+    if (count < 1 || !ctxs || !ctxs[0] || !configs || !n || !eloc_out) return NQS_ERR_INVALID_ARG;
+    nqs_ctx *lead = ctxs[0];
+    if (int rc = check_ctx(lead)) return rc;
+    if (!valid_precision(prec)) return fail(lead, NQS_ERR_INVALID_ARG, "nqs_local_energy_multi: bad precision");
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i] || ctxs[i]->device != lead->device || n[i] < 0 || (n[i] > 0 && (!configs[i] || !eloc_out[i])))
+            return fail(lead, NQS_ERR_INVALID_ARG, "nqs_local_energy_multi: bad context or arrays");
+    }
+    LaunchEnv env = env_of(lead);
+    if (prec != NQS_BF16) {
+        // CUDA-core precisions: one launch per problem, all on the lead stream
+        for (int i = 0; i < count; ++i) {
+            nqs_ctx *c = ctxs[i];
+            DeviceParams dp;
+            dp.p64 = c->params;
+            dp.p32 = c->params32;
+            if (prec == NQS_FP32) {
+                launch_convert_params(c->params, c->params32, c->p.P, lead->stream);
+                ++lead->launches;
+            }
+            const double *lp = logpsi ? logpsi[i] : nullptr;
+            if (int rc = launch_eloc_plain(c->p, prec, dp, configs[i], lp, n[i], eloc_out[i], env)) return rc;
+        }
+        return NQS_OK;
+    }
+    // tensor cores: one grouped launch per channel count
+    for (int i = 0; i < count; ++i)
+        if (ctxs[i]->p.C != 16 && ctxs[i]->p.C != 32)
+            return fail(lead, NQS_ERR_UNSUPPORTED, "the tensor-core path needs 16 or 32 channels");
+    std::vector<TcMultiItem> items;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int C = pass == 0 ? 16 : 32;
+        items.clear();
+        for (int i = 0; i < count; ++i) {
+            nqs_ctx *c = ctxs[i];
+            if (c->p.C != C) continue;
+            if (int rc = launch_tc_pack(c->p, c->params, c->packed, env)) return rc;
+            TcMultiItem it;
+            it.p = c->p;
+            it.packed = c->packed;
+            it.configs = configs[i];
+            it.logpsi = logpsi ? logpsi[i] : nullptr;
+            it.n = n[i];
+            it.out = eloc_out[i];
+            items.push_back(it);
+        }
+        if (items.empty()) continue;
+        const size_t need = tc_multi_table_bytes((int)items.size());
+        if (need > lead->multi_table_bytes) {
+            cudaError_t e = cudaStreamSynchronize(lead->stream);
+            if (e != cudaSuccess) return cuda_fail(lead, e, "stream sync");
+            cudaFree(lead->multi_table);
+            lead->multi_table = nullptr;
+            lead->multi_table_bytes = 0;
+            e = cudaMalloc(&lead->multi_table, need);
+            if (e != cudaSuccess) return cuda_fail(lead, e, "grouped table allocation");
+            lead->multi_table_bytes = need;
+        }
+        if (int rc = launch_eloc_tc_multi(items.data(), (int)items.size(), lead->multi_table, env)) return rc;
+        // the next pass reuses the table: order it after this launch (same stream)
+    }
+    return NQS_OK;
 }
 
 int64_t nqs_kernel_launches(const nqs_ctx *c) { return c ? c->launches : -1; }

@@ -218,6 +218,73 @@ __device__ inline int enumerate_connected(const Problem &p, const int8_t *sigma,
     return count;
 }
 
+// Electron counts along the snake path for the t-J hop signs:
+// cum_snake[q] = electrons at snake positions < q (q = 0..N). All threads.
+__device__ inline void snake_prefix(const Problem &p, const int8_t *sigma, int *cum_snake, EnumScratch &es) {
+    int base = 0;
+    for (int q0 = 0; q0 < p.N; q0 += blockDim.x) {
+        const int q = q0 + threadIdx.x;
+        const int occ = (q < p.N) ? (sigma[snake_site(q, p.L)] != 0) : 0;
+        int tot;
+        const int off = block_exclusive_scan(occ, es.iscr, &tot);
+        if (q < p.N) cum_snake[q] = base + off;
+        base += tot;
+    }
+    if (threadIdx.x == 0) cum_snake[p.N] = base;
+    __syncthreads();
+}
+
+// Connected configurations from bonds [b_begin, b_end) only, in bond order
+// (same rules as enumerate_connected); *hdiag receives the diagonal part of
+// those bonds. For t-J, cum_snake must hold snake_prefix of sigma.
+__device__ inline int enumerate_range(const Problem &p, const int8_t *sigma, int b_begin, int b_end, int16_t *ci,
+                                      int16_t *cj, double *ch, double *hdiag, const int *cum_snake, EnumScratch &es) {
+    double dsum = 0.0;
+    int count = 0;
+    for (int b0 = b_begin; b0 < b_end; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        int flag = 0;
+        int i = 0, j = 0;
+        double h = 0.0;
+        if (b < b_end) {
+            bool nnn;
+            bond_sites(p, b, i, j, nnn);
+            const int si = sigma[i], sj = sigma[j];
+            if (p.model == NQS_MODEL_J1J2) {
+                const double Jb = nnn ? p.J2 : p.J1;
+                dsum += Jb * (double)(si * sj) * 0.25;
+                if (si != sj) {
+                    flag = 1;
+                    h = 0.5 * Jb;
+                    if (p.sign_rule && !nnn) h = -h;
+                }
+            } else {
+                if (si != 0 && sj != 0) {
+                    dsum += p.J * ((double)(si * sj) * 0.25 - 0.25);
+                    if (si != sj) { flag = 1; h = 0.5 * p.J; }
+                } else if ((si == 0) != (sj == 0)) {
+                    flag = 1;
+                    const int pi = snake_pos(i, p.L), pj = snake_pos(j, p.L);
+                    const int lo = pi < pj ? pi : pj, hi = pi < pj ? pj : pi;
+                    h = ((cum_snake[hi] - cum_snake[lo + 1]) & 1) ? p.t : -p.t;
+                }
+            }
+        }
+        int tot;
+        const int off = block_exclusive_scan(flag, es.iscr, &tot);
+        if (flag) {
+            ci[count + off] = (int16_t)i;
+            cj[count + off] = (int16_t)j;
+            ch[count + off] = h;
+        }
+        count += tot;
+    }
+    const double d = block_sum(dsum, es.dscr);
+    if (hdiag) *hdiag = d;
+    __syncthreads();
+    return count;
+}
+
 __device__ __forceinline__ double silu_d(double z) { return z / (1.0 + exp(-z)); }
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
 

@@ -27,6 +27,8 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <vector>
+
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -56,6 +58,11 @@ struct TcPlan {
 
 __host__ __device__ inline uint32_t al16(uint32_t v) { return (v + 15u) & ~15u; }
 
+// Bonds enumerated per chunk by the local-energy kernels (all of them up to
+// 16 x 16 J1-J2; larger lattices are processed chunk by chunk).
+constexpr int kBondChunk = 1024;
+__host__ __device__ inline int bond_chunk(const Problem &p) { return p.n_bonds < kBondChunk ? p.n_bonds : kBondChunk; }
+
 struct TcShared {
     unsigned char *base;
     uint64_t *bar_w;             // [2] weight buffers
@@ -71,10 +78,15 @@ struct TcShared {
 };
 
 struct TcState {        // per-CTA pipeline state (all threads keep identical copies)
-    uint32_t layers[kMaxSlots];   // layers completed per slot (tile-barrier parity)
-    uint32_t wseq;                // weight load used by the next forward's layer 0
-    uint32_t wissued;             // weight loads issued so far
+    uint32_t tphase;    // parity of tile barrier t of slot s at bit s * kMaxTiles + t
+    uint32_t wseq;      // weight load used by the next forward's layer 0
+    uint32_t wissued;   // weight loads issued so far
+    uint32_t wbase;     // first weight load of the bound problem (load q holds layer (q - wbase) mod n_layers)
 };
+
+// Barriers, TMEM address and abort flag sit at a fixed offset (0) so that a
+// block can re-bind to another problem without re-initialising them.
+constexpr uint32_t kBarBytes = 8 * (2 + kMaxSlots * kMaxTiles) + 16;
 
 __device__ __forceinline__ uint32_t act_addr(const TcPlan &pl, const TcShared &sh, int slot, int b) {
     return ptx::smem_u32(sh.base + pl.o_act + (uint32_t)(slot * 2 + b) * pl.act_bytes);
@@ -84,10 +96,10 @@ __device__ __forceinline__ const unsigned char *tc_layer_weights(const TcPlan &p
     return packed + pl.f32_bytes + (l == 0 ? 0 : pl.w0bytes + (size_t)(l - 1) * pl.wbytes);
 }
 
-// Issue the bulk copy of weight-load number q (layer q mod n_layers).
+// Issue the bulk copy of weight-load number q (layer (q - wbase) mod n_layers).
 __device__ __forceinline__ void issue_weight_load(const TcPlan &pl, const TcShared &sh, const unsigned char *packed,
-                                                  uint32_t q) {
-    const int l = (int)(q % (uint32_t)pl.n_layers);
+                                                  uint32_t q, uint32_t wbase) {
+    const int l = (int)((q - wbase) % (uint32_t)pl.n_layers);
     const int b = q & 1;
     const uint32_t bytes = l == 0 ? pl.w0bytes : pl.wbytes;
     unsigned char *dst = sh.base + (b ? pl.o_w1 : pl.o_w0);
@@ -203,7 +215,7 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
         if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
             // the last slot prefetches the next load into the other buffer:
             // its previous user (load q - 1) has completed for every slot
-            if (iw == 0 && slot == pl.slots - 1) issue_weight_load(pl, sh, packed, q + 1);
+            if (iw == 0 && slot == pl.slots - 1) issue_weight_load(pl, sh, packed, q + 1, st.wbase);
             ptx::tc_fence_after();
             const uint32_t tmem = *sh.tmem_addr + (uint32_t)(slot * pl.slot_cols);
             const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
@@ -252,7 +264,6 @@ template <int C>
 __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st, int slot, int l, int *err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
     const bool last = l == pl.n_layers - 1;
-    const uint32_t parity = st.layers[slot] & 1u;
     const uint32_t tmem = *sh.tmem_addr + (uint32_t)(slot * pl.slot_cols);
     const float *bias = sh.f32 + l * C;
     const float *wa = sh.f32 + pl.n_layers * C;
@@ -260,6 +271,7 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
     float *contrib = reinterpret_cast<float *>(sh.base + pl.o_act + (uint32_t)(slot * 2 + (l & 1)) * pl.act_bytes);
     bool ok = true;
     for (int t = warp >> 2; warp < kEpiWarps && t < pl.n_tiles; t += kEpiWarps / 4) {
+        const uint32_t parity = (st.tphase >> (slot * kMaxTiles + t)) & 1u;
         const bool got = wait_or_abort(&sh.bar_tile[slot * kMaxTiles + t], parity, sh.abort_flag);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // reconverges the warp
         ptx::tc_fence_after();
@@ -293,7 +305,7 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
         }
     }
     if (!ok) raise_abort(sh, err);
-    st.layers[slot] += 1;
+    st.tphase ^= ((1u << pl.n_tiles) - 1u) << (slot * kMaxTiles);
     ptx::tc_fence_before();
     ptx::fence_async_smem();
     __syncthreads();
@@ -346,19 +358,13 @@ __device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned 
 }
 
 // ---------------------------------------------------------------- kernel prologue / epilogue
-__device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, const unsigned char *packed,
-                         TcState &st) {
+// Once per block: barriers (fixed offset 0), tensor memory.
+__device__ void tc_init(TcShared &sh, unsigned char *smem, uint32_t tmem_cols, TcState &st) {
     sh.base = smem;
-    sh.bar_w = reinterpret_cast<uint64_t *>(smem + pl.o_bar);
+    sh.bar_w = reinterpret_cast<uint64_t *>(smem);
     sh.bar_tile = sh.bar_w + 2;
-    sh.tmem_addr = reinterpret_cast<uint32_t *>(smem + pl.o_bar + 8 * (2 + kMaxSlots * kMaxTiles));
-    sh.abort_flag = reinterpret_cast<int *>(smem + pl.o_bar + 8 * (2 + kMaxSlots * kMaxTiles) + 4);
-    sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
-    sh.spad = reinterpret_cast<int8_t *>(smem + pl.o_spad);
-    sh.rowtab = reinterpret_cast<const uint2 *>(smem + pl.o_rowtab);
-    sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
-    sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
-    sh.res = reinterpret_cast<double *>(smem + pl.o_res);
+    sh.tmem_addr = reinterpret_cast<uint32_t *>(smem + 8 * (2 + kMaxSlots * kMaxTiles));
+    sh.abort_flag = reinterpret_cast<int *>(smem + 8 * (2 + kMaxSlots * kMaxTiles) + 4);
     if (threadIdx.x == 0) {
         ptx::mbar_init(&sh.bar_w[0], 1);
         ptx::mbar_init(&sh.bar_w[1], 1);
@@ -366,6 +372,30 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
         *sh.abort_flag = 0;
         ptx::fence_mbar_init();
     }
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        ptx::tmem_alloc(sh.tmem_addr, tmem_cols);
+        ptx::tmem_relinquish();
+    }
+    st.tphase = 0;
+    st.wseq = 0;
+    st.wissued = 0;
+    st.wbase = 0;
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+}
+
+// Bind the block to one problem: shared-memory carve-up, parameters,
+// destination tables, zeroed buffers, first weight load.
+__device__ void tc_bind(const TcPlan &pl, TcShared &sh, const unsigned char *packed, TcState &st) {
+    unsigned char *smem = sh.base;
+    sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
+    sh.spad = reinterpret_cast<int8_t *>(smem + pl.o_spad);
+    sh.rowtab = reinterpret_cast<const uint2 *>(smem + pl.o_rowtab);
+    sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
+    sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
+    sh.res = reinterpret_cast<double *>(smem + pl.o_res);
     const float *src = reinterpret_cast<const float *>(packed);
     for (uint32_t i = threadIdx.x; i < pl.f32_count; i += blockDim.x) sh.f32[i] = src[i];
     // destination table of every output row: main row and periodic images
@@ -388,39 +418,46 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
         const int n = images(pl.L, pl.Lp, s % pl.L, s / pl.L, pos);
         sitetab[s] = pack4(pos, n);
     }
-    // zero the activation buffers and padded spins once: rows outside the
-    // lattice are read by discarded output rows only, but keep them finite
+    // zero the activation buffers and padded spins: rows outside the lattice
+    // are read by discarded output rows only, but keep them finite
     for (uint32_t i = threadIdx.x; i < pl.slots * 2 * pl.act_bytes / 4; i += blockDim.x)
         reinterpret_cast<uint32_t *>(smem + pl.o_act)[i] = 0u;
     for (uint32_t i = threadIdx.x; i < (uint32_t)(pl.slots * pl.Lp * pl.Lp * pl.G); i += blockDim.x) sh.spad[i] = 0;
     ptx::fence_async_smem();
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) {
-        ptx::tmem_alloc(sh.tmem_addr, pl.tmem_cols);
-        ptx::tmem_relinquish();
-    }
-    if (threadIdx.x == 0) issue_weight_load(pl, sh, packed, 0);
-    for (int s = 0; s < kMaxSlots; ++s) st.layers[s] = 0;
-    st.wseq = 0;
-    st.wissued = 1;
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
+    st.wbase = st.wissued;
+    st.wseq = st.wissued;
+    if (threadIdx.x == 0) issue_weight_load(pl, sh, packed, st.wissued, st.wbase);
+    st.wissued += 1;
 }
 
-__device__ void tc_teardown(const TcPlan &pl, TcShared &sh, TcState &st) {
+// Wait for prefetched weight loads nobody will consume (before re-binding
+// or exiting), so no copy is in flight into the buffers.
+__device__ void tc_unbind(TcShared &sh, TcState &st) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // prefetched weight loads that nobody consumed
+    if (threadIdx.x == 0)
         for (uint32_t q = st.wseq; q < st.wissued; ++q) ptx::mbar_wait(&sh.bar_w[q & 1], (q >> 1) & 1);
-    }
+    st.wseq = st.wissued;
+    __syncthreads();
+}
+
+__device__ void tc_fini(TcShared &sh, TcState &st, uint32_t tmem_cols) {
+    tc_unbind(sh, st);
     ptx::tc_fence_before();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(*sh.tmem_addr, pl.tmem_cols);
+        ptx::tmem_dealloc(*sh.tmem_addr, tmem_cols);
     }
 }
+
+__device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, const unsigned char *packed,
+                         TcState &st) {
+    tc_init(sh, smem, pl.tmem_cols, st);
+    tc_bind(pl, sh, packed, st);
+}
+
+__device__ void tc_teardown(const TcPlan &pl, TcShared &sh, TcState &st) { tc_fini(sh, st, pl.tmem_cols); }
 
 // ---------------------------------------------------------------- kernels
 template <int C>
@@ -450,40 +487,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) logpsi_tc_kernel(TcPlan pl, con
     tc_teardown(pl, sh, st);
 }
 
+// Local energy of one configuration (Sec. 5.4.1): enumerate its connected
+// configurations, evaluate sigma and all of them in groups, then
+// E_loc = H_diag + sum_k H_k exp((a'_k - a) + i (phi'_k - phi)) in float64,
+// every term of the sample at once, fixed-order block reduction.
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Problem p, const unsigned char *packed,
-                                                                 const int8_t *configs, const double *logpsi,
-                                                                 int64_t n, double *out, int *err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    TcShared sh;
-    TcState st;
-    tc_setup(pl, sh, smem, packed, st);
-    const int G = pl.G, N = pl.N, per = G * pl.slots;
-    unsigned char *ex = smem + pl.o_extra;
+__device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &sh, TcState &st,
+                            const unsigned char *packed, const int8_t *cfg, const double *logpsi_s, double *out_s,
+                            int *err) {
+    const int G = pl.G, N = pl.N, per = G * pl.slots, chunk = bond_chunk(p);
+    unsigned char *ex = sh.base + pl.o_extra;
     int8_t *sigma = reinterpret_cast<int8_t *>(ex);
     int16_t *ci = reinterpret_cast<int16_t *>(ex + al16(N));
-    int16_t *cj = ci + p.n_bonds;
-    double *ch = reinterpret_cast<double *>(ex + al16(N) + al16(4 * p.n_bonds));
-    int *cum = reinterpret_cast<int *>(ch + p.n_bonds);
-    EnumScratch *scr = reinterpret_cast<EnumScratch *>(ex + al16(N) + al16(4 * p.n_bonds) + al16(8 * p.n_bonds) +
+    int16_t *cj = ci + chunk;
+    double *ch = reinterpret_cast<double *>(ex + al16(N) + al16(4 * chunk));
+    int *cum = reinterpret_cast<int *>(ch + chunk);
+    EnumScratch *scr = reinterpret_cast<EnumScratch *>(ex + al16(N) + al16(4 * chunk) + al16(8 * chunk) +
                                                        al16(4 * (N + 1)));
     double *ref = reinterpret_cast<double *>(scr + 1);   // a0, phi0
-    double *lp = ref + 4;                                 // [n_bonds + 1][2]: (a, phi) of every list entry
-    const int recompute = logpsi == nullptr;
-    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
-        for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = configs[s * N + r];
-        __syncthreads();
+    double *lp = ref + 4;                                 // [chunk + 1][2]: (a, phi) of every list entry
+    const int recompute = logpsi_s == nullptr;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = cfg[r];
+    __syncthreads();
+    if (p.model == NQS_MODEL_TJ) snake_prefix(p, sigma, cum, *scr);
+    if (threadIdx.x == 0 && !recompute) { ref[0] = logpsi_s[0]; ref[1] = logpsi_s[1]; }
+    __syncthreads();
+    // bonds in chunks (one chunk unless the lattice is large); running float64
+    // sums of the diagonal and of the off-diagonal terms, identical in every thread
+    double hd_tot = 0.0, sr_tot = 0.0, si_tot = 0.0;
+    for (int b0 = 0; b0 < p.n_bonds; b0 += chunk) {
         double hd;
-        const int nconn = enumerate_connected(p, sigma, ci, cj, ch, &hd, cum, *scr);
-        if (threadIdx.x == 0 && !recompute) { ref[0] = logpsi[2 * s]; ref[1] = logpsi[2 * s + 1]; }
-        __syncthreads();
-        const int n_entries = nconn + recompute;
-        bool ok = true;
+        const int nconn = enumerate_range(p, sigma, b0, min(p.n_bonds, b0 + chunk), ci, cj, ch, &hd, cum, *scr);
+        hd_tot += hd;
+        const int lead = (recompute && b0 == 0) ? 1 : 0;   // sigma itself evaluated first
+        const int n_entries = nconn + lead;
         for (int e0 = 0; e0 < n_entries; e0 += per) {
             const int cnt = min(per, n_entries - e0);
             for (int r = threadIdx.x; r < per * N; r += blockDim.x) {
                 const int c = r / N, site = r - c * N;
-                const int k = e0 + c - recompute;
+                const int k = e0 + c - lead;
                 int v = sigma[site];
                 if (c < cnt && k >= 0) {
                     const int i = ci[k], j = cj[k];
@@ -493,38 +535,99 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Probl
                 sh.spins[r] = (int8_t)v;
             }
             __syncthreads();
-            if (!tc_forward<C>(pl, sh, packed, st, err)) { ok = false; break; }
+            if (!tc_forward<C>(pl, sh, packed, st, err)) return false;
             if (threadIdx.x < cnt) {
                 const int c = threadIdx.x, sl = c / G, g = c - sl * G;
                 lp[2 * (e0 + c)] = sh.res[sl * 2 * G + g];
                 lp[2 * (e0 + c) + 1] = sh.res[sl * 2 * G + G + g];
             }
         }
-        if (!ok) break;
         __syncthreads();
-        if (recompute && threadIdx.x == 0) { ref[0] = lp[0]; ref[1] = lp[1]; }
+        if (lead && threadIdx.x == 0) { ref[0] = lp[0]; ref[1] = lp[1]; }
         __syncthreads();
-        // E_loc = H_diag + sum_k H_k exp((a'_k - a) + i (phi'_k - phi)) in float64,
-        // all terms of the sample at once, fixed-order block reduction
         double tr = 0.0, ti = 0.0;
         for (int k = threadIdx.x; k < nconn; k += blockDim.x) {
-            const double m = ch[k] * exp(lp[2 * (k + recompute)] - ref[0]);
+            const double m = ch[k] * exp(lp[2 * (k + lead)] - ref[0]);
             double sn, cs;
-            sincos(lp[2 * (k + recompute) + 1] - ref[1], &sn, &cs);
+            sincos(lp[2 * (k + lead) + 1] - ref[1], &sn, &cs);
             tr = fma(m, cs, tr);
             ti = fma(m, sn, ti);
         }
-        const double sr = block_sum(tr, scr->dscr);
-        const double si = block_sum(ti, scr->dscr);
-        if (threadIdx.x == 0) {
-            const double er = hd + sr, ei = si;
-            out[2 * s] = er;
-            out[2 * s + 1] = ei;
-            if (!isfinite(er) || !isfinite(ei)) atomicOr(err, ERRBIT_NONFINITE);
-        }
-        __syncthreads();
+        sr_tot += block_sum(tr, scr->dscr);
+        si_tot += block_sum(ti, scr->dscr);
     }
+    if (threadIdx.x == 0) {
+        const double er = hd_tot + sr_tot, ei = si_tot;
+        out_s[0] = er;
+        out_s[1] = ei;
+        if (!isfinite(er) || !isfinite(ei)) atomicOr(err, ERRBIT_NONFINITE);
+    }
+    __syncthreads();
+    return true;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Problem p, const unsigned char *packed,
+                                                                 const int8_t *configs, const double *logpsi,
+                                                                 int64_t n, double *out, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    TcShared sh;
+    TcState st;
+    tc_setup(pl, sh, smem, packed, st);
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
+        if (!eloc_sample<C>(pl, p, sh, st, packed, configs + s * p.N, logpsi ? logpsi + 2 * s : nullptr, out + 2 * s,
+                            err))
+            break;
     tc_teardown(pl, sh, st);
+}
+
+// One problem of a grouped local-energy launch.
+struct TcRequest {
+    TcPlan pl;
+    Problem p;
+    const unsigned char *packed;
+    const int8_t *configs;
+    const double *logpsi;
+    double *out;
+    int64_t n, start;   // samples, index of the first sample in the launch
+};
+
+// Local energies of several problems (same channel count) in one launch:
+// blocks take samples one at a time from a global counter in problem-major
+// order and re-bind their shared-memory plan when the problem changes.
+template <int C>
+__global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_multi_kernel(const TcRequest *reqs, int nreq, int64_t total,
+                                                                       uint32_t tmem_cols, unsigned long long *counter,
+                                                                       int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ long long grab;
+    TcShared sh;
+    TcState st;
+    tc_init(sh, smem, tmem_cols, st);
+    int cur = -1;
+    TcPlan pl;
+    Problem p;
+    while (true) {
+        if (threadIdx.x == 0) grab = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t g = grab;
+        __syncthreads();
+        if (g >= total) break;
+        int r = 0;
+        while (r + 1 < nreq && reqs[r + 1].start <= g) ++r;
+        if (r != cur) {
+            if (cur >= 0) tc_unbind(sh, st);
+            pl = reqs[r].pl;
+            p = reqs[r].p;
+            tc_bind(pl, sh, reqs[r].packed, st);
+            cur = r;
+        }
+        const int64_t s = g - reqs[r].start;
+        const double *lps = reqs[r].logpsi ? reqs[r].logpsi + 2 * s : nullptr;
+        if (!eloc_sample<C>(pl, p, sh, st, reqs[r].packed, reqs[r].configs + s * p.N, lps, reqs[r].out + 2 * s, err))
+            break;
+    }
+    tc_fini(sh, st, tmem_cols);
 }
 
 __device__ __forceinline__ int neighbour_dir_tc(int i, int d, int L) {
@@ -714,7 +817,8 @@ bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_by
     uint32_t cols = 32;
     while (cols < (uint32_t)slots * pl.slot_cols) cols <<= 1;
     pl.tmem_cols = cols;
-    uint32_t o = 0;
+    uint32_t o = kBarBytes;
+    pl.o_bar = 0;
     pl.o_act = o; o = al16(o + (uint32_t)slots * 2u * pl.act_bytes);
     pl.o_w0 = o; o = al16(o + pl.wbytes);
     pl.o_w1 = o; o = al16(o + pl.wbytes);
@@ -724,7 +828,6 @@ bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_by
     pl.o_spad = o; o = al16(o + slots * pl.Lp * pl.Lp * G);
     pl.o_spins = o; o = al16(o + slots * G * p.N);
     pl.o_res = o; o = al16(o + 16 * slots * G);
-    pl.o_bar = o; o = al16(o + 8 * (2 + kMaxSlots * kMaxTiles) + 8);
     pl.o_extra = o; o = al16(o + extra_bytes);
     // co-resident blocks must not ask for more than the SM's 512 TMEM
     // columns together: pad shared memory to cap residency
@@ -740,8 +843,9 @@ bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_by
 }
 
 int eloc_extra(const Problem &p) {
-    return (int)(al16(p.N) + al16(4 * p.n_bonds) + al16(8 * p.n_bonds) + al16(4 * (p.N + 1)) + sizeof(EnumScratch) +
-                 4 * sizeof(double) + 16 * (p.n_bonds + 1));
+    const int chunk = bond_chunk(p);
+    return (int)(al16(p.N) + al16(4 * chunk) + al16(8 * chunk) + al16(4 * (p.N + 1)) + sizeof(EnumScratch) +
+                 4 * sizeof(double) + 16 * (chunk + 1));
 }
 
 int sample_extra(const Problem &p, int G, int slots) {
@@ -870,6 +974,53 @@ int launch_eloc_tc(const Problem &p, const double *, const void *packed, const i
                                                       env.err);
     });
     return check(env, "eloc_tc_kernel");
+}
+
+size_t tc_multi_table_bytes(int count) { return 256 + sizeof(TcRequest) * (size_t)count; }
+
+int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, const LaunchEnv &env) {
+    if (count <= 0) return NQS_OK;
+    const int C = items[0].p.C;
+    std::vector<TcRequest> reqs((size_t)count);
+    uint32_t smem = 0, cols = 32;
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const Problem &p = items[i].p;
+        std::string why;
+        TcPlan pl;
+        if (p.C != C || !tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, &pl, &why)) {
+            *env.msg = p.C != C ? std::string("grouped local energy needs one channel count per launch") : why;
+            return NQS_ERR_UNSUPPORTED;
+        }
+        reqs[i].pl = pl;
+        reqs[i].p = p;
+        reqs[i].packed = (const unsigned char *)items[i].packed;
+        reqs[i].configs = items[i].configs;
+        reqs[i].logpsi = items[i].logpsi;
+        reqs[i].out = items[i].out;
+        reqs[i].n = items[i].n;
+        reqs[i].start = total;
+        total += items[i].n;
+        smem = std::max(smem, pl.total);
+        cols = std::max(cols, pl.tmem_cols);
+    }
+    if (total == 0) return NQS_OK;
+    while (cols * (233472u / (smem + 1024u)) > 512u) smem += 1024u;
+    if (smem > env.max_smem) { *env.msg = "grouped plan exceeds the shared-memory limit"; return NQS_ERR_UNSUPPORTED; }
+    unsigned long long *counter = (unsigned long long *)dev_table;
+    TcRequest *dreqs = (TcRequest *)((unsigned char *)dev_table + 256);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), env.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dreqs, reqs.data(), sizeof(TcRequest) * (size_t)count, cudaMemcpyHostToDevice, env.stream);
+    if (e != cudaSuccess) { *env.msg = std::string("grouped table: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, env.num_sms));
+    NQS_TC_DISPATCH(C, {
+        auto k = eloc_tc_multi_kernel<CC>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { *env.msg = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
+        k<<<grid, kTcThreads, smem, env.stream>>>(dreqs, count, total, cols, counter, env.err);
+    });
+    return check(env, "eloc_tc_multi_kernel");
 }
 
 int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_t *chains, int n_chains,

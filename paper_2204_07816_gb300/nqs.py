@@ -24,7 +24,7 @@ MODEL = {'j1j2': 0, 'tj': 1}
 
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
-           'nqs_connected', 'nqs_local_energy', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
+           'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
            'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve')
 
 
@@ -63,6 +63,7 @@ def load(path=LIB_PATH):
         'nqs_logpsi': (ctypes.c_int, [P, P, I64, P, I32]),
         'nqs_connected': (ctypes.c_int, [P, P, I64, I32, P, P, P, P]),
         'nqs_local_energy': (ctypes.c_int, [P, P, P, I64, P, I32]),
+        'nqs_local_energy_multi': (ctypes.c_int, [P, I32, P, P, P, P, I32]),
         'nqs_sample': (ctypes.c_int, [P, I32, I32, I32, I32, P, P, I32]),
         'nqs_get_chains': (ctypes.c_int, [P, I32, P, ctypes.POINTER(U64)]),
         'nqs_set_chains': (ctypes.c_int, [P, I32, P, U64]),
@@ -109,6 +110,26 @@ def make_problem(model='j1j2', L=4, J1=1.0, J2=0.5, t=1.0, J=0.4, n_up=None, n_d
 
 def nqs_param_count(problem):
     return load().nqs_param_count(ctypes.byref(problem))
+
+
+def local_energy_multi(contexts, configs, precision='bf16', outs=None, logpsi=None):
+    """nqs_local_energy_multi: E_loc of several contexts' configurations in
+    one pass, enqueued on the first context's stream. Returns the list of
+    [n_i, 2] float64 outputs."""
+    lib = load()
+    k = len(contexts)
+    if outs is None:
+        outs = [torch.empty((c.shape[0], 2), dtype=torch.float64, device=c.device) for c in configs]
+    Arr = ctypes.c_void_p * k
+    ctx_arr = Arr(*[c.ctx.value for c in contexts])
+    cfg_arr = Arr(*[ctx._configs(c).value for ctx, c in zip(contexts, configs)])
+    out_arr = Arr(*[_ptr(o, torch.float64, 'out').value for o in outs])
+    lp_arr = Arr(*[_ptr(l, torch.float64, 'logpsi').value for l in logpsi]) if logpsi is not None else None
+    n_arr = (ctypes.c_int64 * k)(*[c.shape[0] for c in configs])
+    rc = lib.nqs_local_energy_multi(ctx_arr, k, cfg_arr, lp_arr, n_arr, out_arr, _prec(precision))
+    if rc != NQS_OK:
+        raise NQSError(rc, lib.nqs_last_error(contexts[0].ctx).decode())
+    return outs
 
 
 def nqs_logpsi_grad_noalloc(problem, params, configs, O_out, precision='fp64', stream=None):
