@@ -44,7 +44,55 @@ def parse():
     ap.add_argument('--oracle-samples', type=int, default=256, help='bounded sample for the CPU oracle')
     ap.add_argument('--profile-eloc', type=int, default=0, metavar='S',
                     help='profiling mode: only run --steps E_loc passes over S uniform random samples')
+    ap.add_argument('--serve', type=int, default=0, metavar='R',
+                    help='serving mode: R Poisson-arriving SR-step requests of mixed lattices (continuous batching)')
     return ap.parse_args()
+
+
+def serve_mix(n_req, seed=0, mean_gap_s=0.3, steps=2):
+    """Seeded request mix: J1-J2 at L in {6, 8, 10, 12, 16, 24, 36} with J2 ~ U[0.4, 0.6] and t-J 12 x 12 at
+    hole doping 1/16 .. 1/8; 6-8 conv layers, 16 or 32 channels (16 at L = 36, where 32 does not fit on chip),
+    2,048-8,192 samples (2,048 for L >= 24); Poisson arrivals."""
+    import numpy as np
+    import nqs_synth
+    from paper_2204_07816_gb300.serving import Request
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    for i in range(n_req):
+        t += rng.exponential(mean_gap_s)
+        n_layers = int(rng.integers(6, 9))
+        if rng.random() < 0.25:
+            n_h = int(rng.choice([10, 12, 14, 16, 18]))
+            ch = int(rng.choice([16, 32]))
+            ns = int(rng.choice([2048, 4096, 8192]))
+            kw = dict(model='tj', L=12, n_up=(144 - n_h) // 2, n_down=(144 - n_h) // 2, n_layers=n_layers, channels=ch)
+            c_in = 3
+        else:
+            L = int(rng.choice([6, 8, 10, 12, 16, 24, 36]))
+            ch = 16 if L == 36 else int(rng.choice([16, 32]))
+            ns = 2048 if L >= 24 else int(rng.choice([2048, 4096, 8192]))
+            kw = dict(model='j1j2', L=L, J2=float(rng.uniform(0.4, 0.6)), n_layers=n_layers, channels=ch)
+            c_in = 1
+        params = nqs_synth.random_params(c_in, ch, n_layers, seed=1000 + i)
+        reqs.append(Request(rid=i, n_samples=ns, n_chains=256, n_steps=steps, seed=i, arrival=t, params=params, **kw))
+    return reqs
+
+
+def run_serve(args):
+    import torch
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300.serving import Server
+    nbuild.build()
+    reqs = serve_mix(args.serve)
+    server = Server(device='cuda', precision='bf16')
+    results, summary = server.run(reqs)
+    per = [{'rid': r.rid, 'model': r.model, 'L': r.L, 'channels': r.channels, 'n_layers': r.n_layers,
+            'samples': r.n_samples, 'arrival_s': round(r.arrival, 3),
+            'step_ms': [round(x * 1e3, 1) for x in results[r.rid].latencies],
+            'cg_iters': results[r.rid].cg_iters} for r in reqs]
+    print(json.dumps({'mode': 'serve', 'metric': 'SR-step latency p50/p99 and throughput, continuous batching',
+                      'summary': summary, 'requests': per, 'dtype': 'bf16', 'data': 'synthetic'}), flush=True)
 
 
 def profile_eloc(args):
@@ -227,6 +275,9 @@ def main():
     if args.profile_eloc:
         profile_eloc(args)
         return
+    if args.serve:
+        run_serve(args)
+        return
     # the oracle's process pool is started before the first GPU call
     rank = int(os.environ.get('RANK', '0'))
     world = int(os.environ.get('WORLD_SIZE', '1'))
@@ -320,13 +371,10 @@ def main():
     ctx, stage, infos, launches, clocks, last = run(args.precision, args.steps, args.warmup, clock)
     step_ms = stage.sum(axis=1)
     eloc_ms = stage[:, 1]
-    # max over ranks of the timed totals
-    tot = torch.tensor([eloc_ms.sum(), step_ms.sum()], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    eloc_total_ms, step_total_ms = tot.tolist()
-    value = n_samples * args.steps * world / (eloc_total_ms / 1000.0)
-    sr_steps_per_s = args.steps * world / (step_total_ms / 1000.0)
+    # max over ranks of the timed totals; whole-job throughput
+    eloc_total_ms, step_total_ms = max_over_ranks([eloc_ms.sum(), step_ms.sum()], dev)
+    value = job_throughput(n_samples * args.steps, world, eloc_total_ms)
+    sr_steps_per_s = job_throughput(args.steps, world, step_total_ms)
 
     # algorithmic FLOPs of one E_loc launch: (n_c + 1) dense forwards per sample
     cfg_last, e_last, _ = last
@@ -418,6 +466,22 @@ def main():
         pool.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum over the ranks of the default process group
+    (identity when there is none)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(units_per_rank, world, max_ms):
+    """Units all ranks processed (each rank the same share) per second of the slowest rank."""
+    return units_per_rank * world / (max_ms / 1000.0)
 
 
 def params_at_step(ctx):

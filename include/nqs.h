@@ -152,10 +152,12 @@ int nqs_local_energy(nqs_ctx *ctx, const int8_t *configs, const double *logpsi, 
  * All work is enqueued on the stream of ctxs[0], which must be on the same
  * device as the others; the caller orders it after the work that produces
  * the inputs (e.g. with events). Host arrays of `count` entries; device
- * arrays as in nqs_local_energy. */
+ * arrays as in nqs_local_energy. max_blocks > 0 caps the grid of the
+ * grouped launch (so that several grouped launches on different streams can
+ * share the SMs); 0 uses every SM. */
 int nqs_local_energy_multi(nqs_ctx *const *ctxs, int32_t count, const int8_t *const *configs,
                            const double *const *logpsi, const int64_t *n, double *const *eloc_out,
-                           int32_t precision);
+                           int32_t precision, int32_t max_blocks);
 
 /* Metropolis exchange sampling from |W(S)|^2 (Sec. 3.2; Sec. 5.4.1
  * "Process-level / thread-level parallel MCMC": many independent chains).

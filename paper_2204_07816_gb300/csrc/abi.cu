@@ -213,7 +213,8 @@ int nqs_destroy(nqs_ctx *c) {
 }
 
 int nqs_local_energy_multi(nqs_ctx *const *ctxs, int32_t count, const int8_t *const *configs,
-                           const double *const *logpsi, const int64_t *n, double *const *eloc_out, int32_t prec) {
+                           const double *const *logpsi, const int64_t *n, double *const *eloc_out, int32_t prec,
+                           int32_t max_blocks) {
     if (count < 1 || !ctxs || !ctxs[0] || !configs || !n || !eloc_out) return NQS_ERR_INVALID_ARG;
     nqs_ctx *lead = ctxs[0];
     if (int rc = check_ctx(lead)) return rc;
@@ -272,7 +273,8 @@ int nqs_local_energy_multi(nqs_ctx *const *ctxs, int32_t count, const int8_t *co
             if (e != cudaSuccess) return cuda_fail(lead, e, "grouped table allocation");
             lead->multi_table_bytes = need;
         }
-        if (int rc = launch_eloc_tc_multi(items.data(), (int)items.size(), lead->multi_table, env)) return rc;
+        if (int rc = launch_eloc_tc_multi(items.data(), (int)items.size(), lead->multi_table, max_blocks, env))
+            return rc;
         // the next pass reuses the table: order it after this launch (same stream)
     }
     return NQS_OK;

@@ -68,7 +68,7 @@ struct TcMultiItem {
     double *out;
 };
 size_t tc_multi_table_bytes(int count);
-int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, const LaunchEnv &env);
+int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, int max_blocks, const LaunchEnv &env);
 int launch_sample_tc(const Problem &p, const double *p64, const void *packed, int8_t *chains, int n_chains,
                      uint64_t step0, uint64_t seed, int spc, int sweeps_between, int burn_in, int8_t *out_cfg,
                      double *out_logpsi, const LaunchEnv &env);

@@ -978,7 +978,7 @@ int launch_eloc_tc(const Problem &p, const double *, const void *packed, const i
 
 size_t tc_multi_table_bytes(int count) { return 256 + sizeof(TcRequest) * (size_t)count; }
 
-int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, const LaunchEnv &env) {
+int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, int max_blocks, const LaunchEnv &env) {
     if (count <= 0) return NQS_OK;
     const int C = items[0].p.C;
     std::vector<TcRequest> reqs((size_t)count);
@@ -1013,7 +1013,8 @@ int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, c
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dreqs, reqs.data(), sizeof(TcRequest) * (size_t)count, cudaMemcpyHostToDevice, env.stream);
     if (e != cudaSuccess) { *env.msg = std::string("grouped table: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, env.num_sms));
+    const int cap = max_blocks > 0 ? std::min(max_blocks, env.num_sms) : env.num_sms;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, cap));
     NQS_TC_DISPATCH(C, {
         auto k = eloc_tc_multi_kernel<CC>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -63,7 +63,7 @@ def load(path=LIB_PATH):
         'nqs_logpsi': (ctypes.c_int, [P, P, I64, P, I32]),
         'nqs_connected': (ctypes.c_int, [P, P, I64, I32, P, P, P, P]),
         'nqs_local_energy': (ctypes.c_int, [P, P, P, I64, P, I32]),
-        'nqs_local_energy_multi': (ctypes.c_int, [P, I32, P, P, P, P, I32]),
+        'nqs_local_energy_multi': (ctypes.c_int, [P, I32, P, P, P, P, I32, I32]),
         'nqs_sample': (ctypes.c_int, [P, I32, I32, I32, I32, P, P, I32]),
         'nqs_get_chains': (ctypes.c_int, [P, I32, P, ctypes.POINTER(U64)]),
         'nqs_set_chains': (ctypes.c_int, [P, I32, P, U64]),
@@ -112,7 +112,7 @@ def nqs_param_count(problem):
     return load().nqs_param_count(ctypes.byref(problem))
 
 
-def local_energy_multi(contexts, configs, precision='bf16', outs=None, logpsi=None):
+def local_energy_multi(contexts, configs, precision='bf16', outs=None, logpsi=None, max_blocks=0):
     """nqs_local_energy_multi: E_loc of several contexts' configurations in
     one pass, enqueued on the first context's stream. Returns the list of
     [n_i, 2] float64 outputs."""
@@ -126,7 +126,7 @@ def local_energy_multi(contexts, configs, precision='bf16', outs=None, logpsi=No
     out_arr = Arr(*[_ptr(o, torch.float64, 'out').value for o in outs])
     lp_arr = Arr(*[_ptr(l, torch.float64, 'logpsi').value for l in logpsi]) if logpsi is not None else None
     n_arr = (ctypes.c_int64 * k)(*[c.shape[0] for c in configs])
-    rc = lib.nqs_local_energy_multi(ctx_arr, k, cfg_arr, lp_arr, n_arr, out_arr, _prec(precision))
+    rc = lib.nqs_local_energy_multi(ctx_arr, k, cfg_arr, lp_arr, n_arr, out_arr, _prec(precision), int(max_blocks))
     if rc != NQS_OK:
         raise NQSError(rc, lib.nqs_last_error(contexts[0].ctx).decode())
     return outs

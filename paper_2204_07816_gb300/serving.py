@@ -4,26 +4,29 @@ independent lattices (a J2 or doping scan at uneven L).
 Every request asks for `n_steps` SR steps of its own problem (Sec. 3.2: MCMC
 by |W|^2, local energies, local derivatives, SR update). The server admits
 requests in arrival order while their device-memory footprint fits the
-budget, keeps each admitted request's parameters and Markov chains resident
-in its own context (one CUDA stream each), and runs ticks: in a tick every
-active request advances by one SR step,
+budget and keeps each admitted request's parameters and Markov chains
+resident in its own context, on its own CUDA stream. Each admitted request
+runs its own loop of SR steps in a host thread:
 
-  1. sampling on each request's own stream,
-  2. ONE grouped local-energy launch over all active requests
-     (nqs_local_energy_multi: per channel count, blocks move from problem
-     to problem), ordered after every request's samples by events,
-  3. local derivatives and the SR solve of each request on its own stream,
-     issued from one host thread per request so that the streams overlap.
+  1. sampling on its stream,
+  2. its local energies are submitted to a shared batcher, which groups
+     every submission pending at that moment into grouped launches
+     (nqs_local_energy_multi: blocks move from problem to problem), one per
+     cost class (lattices up to 16 x 16, larger ones), each launch with a
+     grid share of the SMs proportional to its work so the classes run side
+     by side,
+  3. local derivatives and the SR solve on its stream.
 
-Requests that arrive while others run join at the next tick as soon as the
-memory of finished requests is returned. All reductions in the kernels run
-in a fixed order and the per-configuration results do not depend on what
-else shares a launch, so a request's trajectory is the same alone and in any
-mix. Step latency = from the start of the tick to the end of the request's
-SR solve; the summary reports p50 / p99 over every step of every request and
-the throughput in SR steps and E_loc samples per second.
+A request that arrives while others run is admitted as soon as memory is
+returned by a finished one and joins the next grouped launch. Every kernel
+reduces in a fixed order and per-configuration results do not depend on
+what else shares a launch, so a request's trajectory is the same alone and
+in any mix. Step latency = from the start of a request's step (sampling) to
+the end of its SR update; the summary reports p50 / p99 over every step of
+every request and the throughput in SR steps and E_loc samples per second.
 """
 
+import queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -65,6 +68,13 @@ class Request:
         return nqs.make_problem('tj', self.L, t=self.t, J=self.J, n_up=n_up, n_down=n_down,
                                 n_layers=self.n_layers, channels=self.channels)
 
+    def eloc_cost(self):
+        """Relative cost of one local-energy pass: samples x connected
+        configurations x sites x per-site network work."""
+        N = self.L * self.L
+        bonds = (4 if self.model == 'j1j2' else 2) * N
+        return float(self.n_samples) * bonds * N * self.channels ** 2 * self.n_layers
+
 
 @dataclass
 class RequestResult:
@@ -100,115 +110,182 @@ class _Run:
         self.precision = precision
         self.sr_args = sr_args
         self.stream = torch.cuda.Stream(device)
-        prob = req.problem()
+        self.device = device
         with torch.cuda.stream(self.stream):
-            p0 = req.params
-            if p0 is None:
+            if req.params is None:
                 raise ValueError('request %d has no initial parameters' % req.rid)
-            self.params = torch.tensor(p0, dtype=torch.float64, device=device)
-            self.ctx = nqs.Context(prob, self.params, seed=req.seed, stream=self.stream)
+            self.params = torch.tensor(req.params, dtype=torch.float64, device=device)
+            self.ctx = nqs.Context(req.problem(), self.params, seed=req.seed, stream=self.stream)
             self.eloc = torch.empty((req.n_samples, 2), dtype=torch.float64, device=device)
             self.O = torch.empty((2 * req.n_samples, self.ctx.P), dtype=torch.float64, device=device)
             self.delta = torch.empty(self.ctx.P, dtype=torch.float64, device=device)
         self.spc = req.n_samples // req.n_chains
-        self.steps_done = 0
         self.result = RequestResult(req.rid)
         self.sampled = torch.cuda.Event()
+        self.eloc_done = None
+        self.ready = threading.Event()
         self.cfg = None
+        self.error = None
 
-    def sample(self, burn):
-        with torch.cuda.stream(self.stream):
-            self.cfg, _ = self.ctx.sample(self.req.n_chains, self.spc, 1, burn, self.precision)
-        self.sampled.record(self.stream)
-
-    def finish_step(self, eloc_done, tick_start, t0):
-        """Backward, SR solve and update on this request's stream (runs in a worker thread)."""
-        with torch.cuda.stream(self.stream):
-            self.stream.wait_event(eloc_done)
-            self.ctx.logpsi_grad(self.cfg, self.precision, out=self.O)
-            _, info = self.ctx.sr_solve(self.O, self.eloc, delta=self.delta, apply_update=True, **self.sr_args)
-        self.stream.synchronize()
-        now = time.perf_counter()
-        self.result.latencies.append(now - tick_start)
-        self.result.energies.append(info['energy'])
-        self.result.cg_iters.append(info['iters'])
-        self.steps_done += 1
-        if self.steps_done == self.req.n_steps:
-            self.result.finished_at = now - t0
+    def loop(self, batcher, t0, on_done):
+        try:
+            torch.cuda.set_device(self.device)
+            for step in range(self.req.n_steps):
+                start = time.perf_counter()
+                with torch.cuda.stream(self.stream):
+                    self.cfg, _ = self.ctx.sample(self.req.n_chains, self.spc, 1,
+                                                  self.req.burn_in if step == 0 else 0, self.precision)
+                self.sampled.record(self.stream)
+                self.ready.clear()
+                batcher.submit(self)
+                self.ready.wait()
+                if self.error:
+                    raise self.error
+                with torch.cuda.stream(self.stream):
+                    self.stream.wait_event(self.eloc_done)
+                    self.ctx.logpsi_grad(self.cfg, self.precision, out=self.O)
+                    _, info = self.ctx.sr_solve(self.O, self.eloc, delta=self.delta, apply_update=True, **self.sr_args)
+                self.stream.synchronize()
+                self.result.latencies.append(time.perf_counter() - start)
+                self.result.energies.append(info['energy'])
+                self.result.cg_iters.append(info['iters'])
+            self.result.finished_at = time.perf_counter() - t0
             self.result.params = self.params.detach().cpu().numpy().copy()
+        except Exception as e:      # reported by the server
+            self.error = e
+        finally:
+            on_done(self)
 
     def close(self):
         self.ctx.close()
         del self.O, self.eloc, self.delta, self.cfg
 
 
+class _Batcher:
+    """Groups pending local-energy submissions into grouped launches."""
+
+    SMALL_SITES = 256
+
+    def __init__(self, device, precision, num_sms, window_s=0.0005):
+        self.q = queue.Queue()
+        self.device = device
+        self.precision = precision
+        self.num_sms = num_sms
+        self.window = window_s
+        self.samples = 0
+        self.launches = 0
+        self.stop = False
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def submit(self, run):
+        self.q.put(run)
+
+    def _loop(self):
+        torch.cuda.set_device(self.device)
+        while not self.stop:
+            try:
+                first = self.q.get(timeout=0.05)
+            except queue.Empty:
+                continue
+            batch = [first]
+            time.sleep(self.window)
+            while True:
+                try:
+                    batch.append(self.q.get_nowait())
+                except queue.Empty:
+                    break
+            classes = {}
+            for r in batch:
+                key = (r.req.L * r.req.L > self.SMALL_SITES, r.req.channels)
+                classes.setdefault(key, []).append(r)
+            total = sum(r.req.eloc_cost() for r in batch)
+            for group in classes.values():
+                share = sum(r.req.eloc_cost() for r in group) / total
+                blocks = max(8, int(round(self.num_sms * share))) if len(classes) > 1 else 0
+                lead = group[0]
+                try:
+                    for r in group:
+                        lead.stream.wait_event(r.sampled)
+                    with torch.cuda.stream(lead.stream):
+                        nqs.local_energy_multi([r.ctx for r in group], [r.cfg for r in group], self.precision,
+                                               outs=[r.eloc for r in group], max_blocks=blocks)
+                    done = torch.cuda.Event()
+                    done.record(lead.stream)
+                    self.launches += 1
+                    self.samples += sum(r.req.n_samples for r in group)
+                    for r in group:
+                        r.eloc_done = done
+                except Exception as e:
+                    for r in group:
+                        r.error = e
+                for r in group:
+                    r.ready.set()
+
+
 class Server:
     def __init__(self, device='cuda', hbm_budget_bytes=None, precision='bf16', eps=1e-4, rtol=1e-8,
                  max_iter=10000, lr=0.02):
         self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device('cuda', torch.cuda.current_device())
         if hbm_budget_bytes is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             hbm_budget_bytes = int(free * 0.8)
         self.budget = hbm_budget_bytes
         self.precision = precision
         self.sr_args = dict(eps=eps, rtol=rtol, max_iter=max_iter, lr=lr)
-        self.events = []          # (time, kind, rid) log: 'arrive', 'admit', 'retire'
+        self.events = []          # (time, kind, rid) log: 'admit', 'retire'
 
     def run(self, requests):
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in pending:
             if footprint_bytes(r) > self.budget:
                 raise ValueError('request %d needs more memory than the whole budget' % r.rid)
-        active, results = [], {}
+        num_sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        batcher = _Batcher(self.device, self.precision, num_sms)
+        lock = threading.Lock()
+        finished = []
+        results = {}
+        running = {}
         used = 0
         t0 = time.perf_counter()
-        ticks = 0
-        eloc_samples = 0
-        while pending or active:
-            now = time.perf_counter() - t0
-            # admission in arrival order while the footprint fits
-            while pending and pending[0].arrival <= now and used + footprint_bytes(pending[0]) <= self.budget:
-                req = pending.pop(0)
-                run = _Run(req, self.device, self.precision, self.sr_args)
-                run.result.admitted_at = now
-                used += footprint_bytes(req)
-                active.append(run)
-                self.events.append((now, 'admit', req.rid))
-            if not active:
-                time.sleep(max(0.0, min(0.05, pending[0].arrival - now)))
-                continue
-            tick_start = time.perf_counter()
-            for run in active:
-                run.sample(run.req.burn_in if run.steps_done == 0 else 0)
-            lead = active[0]
-            for run in active:
-                lead.stream.wait_event(run.sampled)
-            with torch.cuda.stream(lead.stream):
-                nqs.local_energy_multi([r.ctx for r in active], [r.cfg for r in active], self.precision,
-                                       outs=[r.eloc for r in active])
-            eloc_done = torch.cuda.Event()
-            eloc_done.record(lead.stream)
-            eloc_samples += sum(r.req.n_samples for r in active)
-            threads = [threading.Thread(target=r.finish_step, args=(eloc_done, tick_start, t0)) for r in active]
-            for th in threads:
-                th.start()
-            for th in threads:
-                th.join()
-            ticks += 1
-            still = []
-            for run in active:
-                if run.steps_done >= run.req.n_steps:
+
+        def on_done(run):
+            with lock:
+                finished.append(run)
+
+        try:
+            while pending or running:
+                now = time.perf_counter() - t0
+                with lock:
+                    done_now, finished[:] = list(finished), []
+                for run in done_now:
+                    running.pop(run.req.rid).join()
+                    if run.error:
+                        raise run.error
                     results[run.req.rid] = run.result
                     used -= footprint_bytes(run.req)
                     run.close()
                     self.events.append((time.perf_counter() - t0, 'retire', run.req.rid))
-                else:
-                    still.append(run)
-            active = still
+                now = time.perf_counter() - t0
+                while pending and pending[0].arrival <= now and used + footprint_bytes(pending[0]) <= self.budget:
+                    req = pending.pop(0)
+                    run = _Run(req, self.device, self.precision, self.sr_args)
+                    run.result.admitted_at = now
+                    used += footprint_bytes(req)
+                    th = threading.Thread(target=run.loop, args=(batcher, t0, on_done), daemon=True)
+                    running[req.rid] = th
+                    self.events.append((now, 'admit', req.rid))
+                    th.start()
+                time.sleep(0.001)
+        finally:
+            batcher.stop = True
+            batcher.thread.join(timeout=5)
         wall = time.perf_counter() - t0
         lat = np.array([x for r in results.values() for x in r.latencies])
         steps = sum(len(r.latencies) for r in results.values())
-        summary = {'requests': len(results), 'sr_steps': steps, 'ticks': ticks, 'wall_s': wall,
-                   'sr_steps_per_s': steps / wall, 'eloc_samples_per_s': eloc_samples / wall,
+        summary = {'requests': len(results), 'sr_steps': steps, 'grouped_launches': batcher.launches,
+                   'wall_s': wall, 'sr_steps_per_s': steps / wall, 'eloc_samples_per_s': batcher.samples / wall,
                    'p50_ms': float(np.percentile(lat, 50) * 1e3), 'p99_ms': float(np.percentile(lat, 99) * 1e3)}
         return results, summary
