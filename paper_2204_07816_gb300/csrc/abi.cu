@@ -143,6 +143,15 @@ int64_t nqs_param_count(const nqs_problem *q) {
     return make_problem(q).P;
 }
 
+int nqs_tc_plan(const nqs_problem *q, int32_t kind, int64_t n, int32_t max_smem_per_block, int32_t num_sms,
+                int32_t *out) {
+    std::string why;
+    if (!out || kind < 0 || kind > 2 || n < 1 || max_smem_per_block <= 0 || num_sms <= 0) return NQS_ERR_INVALID_ARG;
+    if (!valid_problem(q, &why)) return NQS_ERR_INVALID_ARG;
+    if (kind == 2 && n > INT32_MAX) return NQS_ERR_INVALID_ARG;
+    return tc_describe_plan(make_problem(q), kind, n, (size_t)max_smem_per_block, num_sms, out, &why);
+}
+
 int nqs_init(nqs_ctx **out, const nqs_problem *q, double *params, uint64_t seed, void *stream) {
     if (!out) return NQS_ERR_INVALID_ARG;
     *out = nullptr;

@@ -115,6 +115,41 @@ __device__ inline double block_sum(double v, double *scratch) {
     return r;
 }
 
+// Sum over k < n of the pairs value(k) = (x, y), in an order that does not
+// depend on the block size: item k goes to partial sum k mod 128 (items in
+// increasing k), then warp 0 adds the 128 partials in a fixed tree. Needs
+// blockDim.x >= 32; scratch: >= 258 doubles of shared memory. Result valid in
+// every thread.
+template <typename F>
+__device__ inline double2 fixed_order_sum2(int n, F value, double *scratch) {
+    for (int v = threadIdx.x; v < 128; v += blockDim.x) {
+        double x = 0.0, y = 0.0;
+        for (int k = v; k < n; k += 128) {
+            const double2 t = value(k);
+            x += t.x;
+            y += t.y;
+        }
+        scratch[v] = x;
+        scratch[128 + v] = y;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        double x = (scratch[l] + scratch[l + 32]) + (scratch[l + 64] + scratch[l + 96]);
+        double y = (scratch[128 + l] + scratch[160 + l]) + (scratch[192 + l] + scratch[224 + l]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (l == 0) { scratch[256] = x; scratch[257] = y; }
+    }
+    __syncthreads();
+    const double2 r = make_double2(scratch[256], scratch[257]);
+    __syncthreads();
+    return r;
+}
+
 // Exclusive prefix sum of one int flag per thread over the block; returns
 // the thread's offset and writes the block total to *total. scratch: >= 33 ints.
 __device__ inline int block_exclusive_scan(int v, int *scratch, int *total) {
@@ -154,6 +189,17 @@ __device__ inline int block_exclusive_scan(int v, int *scratch, int *total) {
 // >= 33 doubles. All threads of the block must call this.
 struct EnumScratch { int iscr[34]; double dscr[34]; };
 
+// Diagonal element H_{sigma sigma} from integer sums over bonds (exact, so it
+// does not depend on how the bonds are split among threads). J1-J2 (Eq. of
+// the J1-J2 model): s1 = sum over NN bonds of s_i s_j, s2 = the same over NNN
+// bonds, with s = +-1, giving (J1 s1 + J2 s2) / 4. t-J: s1 = sum of s_i s_j
+// over NN bonds holding two electrons, s2 = the number of those bonds, giving
+// J (s1 / 4 - s2 / 4).
+__device__ __forceinline__ double diagonal_element(const Problem &p, int s1, int s2) {
+    if (p.model == NQS_MODEL_J1J2) return 0.25 * (p.J1 * (double)s1 + p.J2 * (double)s2);
+    return p.J * (0.25 * (double)s1 - 0.25 * (double)s2);
+}
+
 __device__ inline int enumerate_connected(const Problem &p, const int8_t *sigma, int16_t *ci, int16_t *cj,
                                           double *ch, double *hdiag, int *cum_snake, EnumScratch &es) {
     const int N = p.N;
@@ -171,7 +217,7 @@ __device__ inline int enumerate_connected(const Problem &p, const int8_t *sigma,
         if (threadIdx.x == 0) cum_snake[N] = base;
         __syncthreads();
     }
-    double dsum = 0.0;
+    int d1 = 0, d2 = 0;   // integer sums of s_i s_j (see diagonal_element)
     int count = 0;
     for (int b0 = 0; b0 < p.n_bonds; b0 += blockDim.x) {
         const int b = b0 + threadIdx.x;
@@ -184,7 +230,7 @@ __device__ inline int enumerate_connected(const Problem &p, const int8_t *sigma,
             const int si = sigma[i], sj = sigma[j];
             if (p.model == NQS_MODEL_J1J2) {
                 const double Jb = nnn ? p.J2 : p.J1;
-                dsum += Jb * (double)(si * sj) * 0.25;
+                if (nnn) d2 += si * sj; else d1 += si * sj;
                 if (si != sj) {
                     flag = 1;
                     h = 0.5 * Jb;
@@ -192,7 +238,8 @@ __device__ inline int enumerate_connected(const Problem &p, const int8_t *sigma,
                 }
             } else {
                 if (si != 0 && sj != 0) {
-                    dsum += p.J * ((double)(si * sj) * 0.25 - 0.25);
+                    d1 += si * sj;
+                    d2 += 1;
                     if (si != sj) { flag = 1; h = 0.5 * p.J; }
                 } else if ((si == 0) != (sj == 0)) {
                     flag = 1;
@@ -212,8 +259,10 @@ __device__ inline int enumerate_connected(const Problem &p, const int8_t *sigma,
         }
         count += tot;
     }
-    const double d = block_sum(dsum, es.dscr);
-    if (hdiag) *hdiag = d;
+    int t1, t2;
+    block_exclusive_scan(d1, es.iscr, &t1);
+    block_exclusive_scan(d2, es.iscr, &t2);
+    if (hdiag) *hdiag = diagonal_element(p, t1, t2);
     __syncthreads();
     return count;
 }
@@ -239,7 +288,7 @@ __device__ inline void snake_prefix(const Problem &p, const int8_t *sigma, int *
 // those bonds. For t-J, cum_snake must hold snake_prefix of sigma.
 __device__ inline int enumerate_range(const Problem &p, const int8_t *sigma, int b_begin, int b_end, int16_t *ci,
                                       int16_t *cj, double *ch, double *hdiag, const int *cum_snake, EnumScratch &es) {
-    double dsum = 0.0;
+    int d1 = 0, d2 = 0;   // integer sums of s_i s_j (see diagonal_element)
     int count = 0;
     for (int b0 = b_begin; b0 < b_end; b0 += blockDim.x) {
         const int b = b0 + threadIdx.x;
@@ -252,7 +301,7 @@ __device__ inline int enumerate_range(const Problem &p, const int8_t *sigma, int
             const int si = sigma[i], sj = sigma[j];
             if (p.model == NQS_MODEL_J1J2) {
                 const double Jb = nnn ? p.J2 : p.J1;
-                dsum += Jb * (double)(si * sj) * 0.25;
+                if (nnn) d2 += si * sj; else d1 += si * sj;
                 if (si != sj) {
                     flag = 1;
                     h = 0.5 * Jb;
@@ -260,7 +309,8 @@ __device__ inline int enumerate_range(const Problem &p, const int8_t *sigma, int
                 }
             } else {
                 if (si != 0 && sj != 0) {
-                    dsum += p.J * ((double)(si * sj) * 0.25 - 0.25);
+                    d1 += si * sj;
+                    d2 += 1;
                     if (si != sj) { flag = 1; h = 0.5 * p.J; }
                 } else if ((si == 0) != (sj == 0)) {
                     flag = 1;
@@ -279,8 +329,10 @@ __device__ inline int enumerate_range(const Problem &p, const int8_t *sigma, int
         }
         count += tot;
     }
-    const double d = block_sum(dsum, es.dscr);
-    if (hdiag) *hdiag = d;
+    int t1, t2;
+    block_exclusive_scan(d1, es.iscr, &t1);
+    block_exclusive_scan(d2, es.iscr, &t2);
+    if (hdiag) *hdiag = diagonal_element(p, t1, t2);
     __syncthreads();
     return count;
 }

@@ -69,6 +69,11 @@ struct TcMultiItem {
 };
 size_t tc_multi_table_bytes(int count);
 int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, int max_blocks, const LaunchEnv &env);
+// Tensor-core plan the launchers choose (host only): kind 0 log psi, 1 local
+// energy, 2 sampler (n = chains). out[8]: G, slots, blocks per SM, epilogue
+// warps, tiles per group, shared bytes per block, TMEM columns, grid.
+int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int num_sms, int32_t *out,
+                     std::string *why);
 int launch_sample_tc(const Problem &p, const double *p64, const void *packed, int8_t *chains, int n_chains,
                      uint64_t step0, uint64_t seed, int spc, int sweeps_between, int burn_in, int8_t *out_cfg,
                      double *out_logpsi, const LaunchEnv &env);

@@ -38,15 +38,27 @@ namespace nqs {
 
 namespace {
 
-constexpr int kEpiWarps = 8;      // epilogue warps: warp w reads TMEM lanes 32 (w % 4) ...; tiles split by w / 4
-constexpr int kIssuers = 2;       // dedicated issuing warps (lane 0 issues tcgen05.mma), after the epilogue warps
-constexpr int kTcThreads = 32 * (kEpiWarps + kIssuers);
+// Warp roles: pl.epi epilogue warps (a multiple of 4; warp w reads TMEM lanes
+// 32 (w % 4) ... and takes tiles w / 4, w / 4 + epi / 4, ...), then kIssuers
+// issuing warps (lane 0 issues tcgen05.mma). The single-problem kernels are
+// compiled for two co-resident blocks per SM (at most 102 registers a
+// thread), so that one block's MMAs run while the other block is between
+// layers or between groups of configurations.
+constexpr int kMaxEpiWarps = 8;
+constexpr int kIssuers = 2;
+constexpr int kTcThreads = 32 * (kMaxEpiWarps + kIssuers);
+// Blocks per SM the log psi / local-energy kernels are compiled for: two for
+// 16 channels (register cap 102), one for 32 channels (two-block plans are
+// slower there, and the uncapped registers are measured 2-3 % faster). The
+// sampler is compiled for two blocks at both widths.
+template <int C> constexpr int kMinBlocks = C == 16 ? 2 : 1;
 constexpr int kMaxTiles = 16;
 constexpr int kMaxSlots = 2;
 constexpr uint32_t kNone = 0xFFFFu;
 
 struct TcPlan {
     int L, Lp, N, G, C, KC, c_in, K0, n_layers, slots;
+    int epi, ctas;       // epilogue warps per block; blocks per SM the plan is sized for
     int count_out, n_tiles, r0, rbuf;
     uint32_t plane, act_bytes, w0bytes, wbytes, tmem_cols, slot_cols;
     // packed parameter image (global): fp32 biases + head, then bf16 operand
@@ -210,8 +222,8 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
                             int l, int *err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = st.wseq + (uint32_t)l;
-    const int iw = warp - kEpiWarps;   // issuer index
-    if (lane == 0 && iw >= 0) {
+    const int iw = warp - pl.epi;   // issuer index
+    if (lane == 0 && iw >= 0 && iw < kIssuers) {
         if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
             // the last slot prefetches the next load into the other buffer:
             // its previous user (load q - 1) has completed for every slot
@@ -269,28 +281,37 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
     const float *wa = sh.f32 + pl.n_layers * C;
     const uint32_t out = act_addr(pl, sh, slot, l & 1);
     float *contrib = reinterpret_cast<float *>(sh.base + pl.o_act + (uint32_t)(slot * 2 + (l & 1)) * pl.act_bytes);
+    // halved biases in registers for 16 channels (for 32 the registers are
+    // kept for two co-resident blocks; the loads stay in the loop)
+    constexpr int HB = C == 16 ? C : 1;
+    float hb[HB];
+#pragma unroll
+    for (int c = 0; c < HB; ++c) hb[c] = 0.5f * bias[c];
     bool ok = true;
-    for (int t = warp >> 2; warp < kEpiWarps && t < pl.n_tiles; t += kEpiWarps / 4) {
+    for (int t = warp >> 2; warp < pl.epi && t < pl.n_tiles; t += pl.epi / 4) {
         const uint32_t parity = (st.tphase >> (slot * kMaxTiles + t)) & 1u;
+        const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
         const bool got = wait_or_abort(&sh.bar_tile[slot * kMaxTiles + t], parity, sh.abort_flag);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // reconverges the warp
         ptx::tc_fence_after();
+        uint32_t r[C / 16][16];
+#pragma unroll
+        for (int h = 0; h < C / 16; ++h)
+            ptx::tmem_ld16_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * C + 16 * h), r[h]);
+        ptx::tmem_wait_ld();
         float v[C];
 #pragma unroll
-        for (int h = 0; h < C / 16; ++h) {
-            float tmp[16];
-            ptx::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * C + 16 * h), tmp);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[16 * h + i] = tmp[i];
-        }
-        const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
+        for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
         const uint32_t main = dst.x & 0xFFFFu;
         if (main == kNone) continue;
         if (!last) {
             uint32_t w[C / 2];
 #pragma unroll
-            for (int c = 0; c < C / 2; ++c)
-                w[c] = ptx::pack_bf16(ptx::silu_fast(v[2 * c] + bias[2 * c]), ptx::silu_fast(v[2 * c + 1] + bias[2 * c + 1]));
+            for (int c = 0; c < C / 2; ++c) {
+                const float h0 = C == 16 ? hb[(2 * c) % HB] : 0.5f * bias[2 * c];
+                const float h1 = C == 16 ? hb[(2 * c + 1) % HB] : 0.5f * bias[2 * c + 1];
+                w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
+            }
             store_rows<C>(pl, out, dst, w);
         } else {
             float ca = 0.f, cp = 0.f;
@@ -318,7 +339,7 @@ __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot) {
     const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act +
                                                            (uint32_t)(slot * 2 + ((pl.n_layers - 1) & 1)) * pl.act_bytes);
     double *res = sh.res + slot * 2 * G;
-    for (int g = warp; g < G; g += kTcThreads / 32) {
+    for (int g = warp; g < G; g += (int)(blockDim.x >> 5)) {
         float sa = 0.f, sp = 0.f;
         for (int site = lane; site < pl.N; site += 32) {
             const int row = (int)(sh.sitetab[site].x & 0xFFFFu) * G + g;
@@ -461,7 +482,7 @@ __device__ void tc_teardown(const TcPlan &pl, TcShared &sh, TcState &st) { tc_fi
 
 // ---------------------------------------------------------------- kernels
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1) logpsi_tc_kernel(TcPlan pl, const unsigned char *packed,
+__global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) logpsi_tc_kernel(TcPlan pl, const unsigned char *packed,
                                                                    const int8_t *configs, int64_t n, double *out,
                                                                    int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -506,6 +527,7 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
                                                        al16(4 * (N + 1)));
     double *ref = reinterpret_cast<double *>(scr + 1);   // a0, phi0
     double *lp = ref + 4;                                 // [chunk + 1][2]: (a, phi) of every list entry
+    double *fsum = lp + 2 * (chunk + 1);                  // [258] fixed-order sum scratch
     const int recompute = logpsi_s == nullptr;
     for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = cfg[r];
     __syncthreads();
@@ -545,16 +567,15 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
         __syncthreads();
         if (lead && threadIdx.x == 0) { ref[0] = lp[0]; ref[1] = lp[1]; }
         __syncthreads();
-        double tr = 0.0, ti = 0.0;
-        for (int k = threadIdx.x; k < nconn; k += blockDim.x) {
+        // off-diagonal terms in an order independent of the block size
+        const double2 tsum = fixed_order_sum2(nconn, [&](int k) {
             const double m = ch[k] * exp(lp[2 * (k + lead)] - ref[0]);
             double sn, cs;
             sincos(lp[2 * (k + lead) + 1] - ref[1], &sn, &cs);
-            tr = fma(m, cs, tr);
-            ti = fma(m, sn, ti);
-        }
-        sr_tot += block_sum(tr, scr->dscr);
-        si_tot += block_sum(ti, scr->dscr);
+            return make_double2(m * cs, m * sn);
+        }, fsum);
+        sr_tot += tsum.x;
+        si_tot += tsum.y;
     }
     if (threadIdx.x == 0) {
         const double er = hd_tot + sr_tot, ei = si_tot;
@@ -567,7 +588,7 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
 }
 
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_kernel(TcPlan pl, Problem p, const unsigned char *packed,
+__global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) eloc_tc_kernel(TcPlan pl, Problem p, const unsigned char *packed,
                                                                  const int8_t *configs, const double *logpsi,
                                                                  int64_t n, double *out, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -640,7 +661,7 @@ __device__ __forceinline__ int neighbour_dir_tc(int i, int d, int L) {
 // Metropolis exchange sampler. Each block owns up to slots * G chains;
 // slot s evaluates the proposals of chains s * G ... s * G + G - 1.
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1) sample_tc_kernel(TcPlan pl, const unsigned char *packed,
+__global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, const unsigned char *packed,
                                                                    int8_t *chains, int n_chains, int per_block,
                                                                    uint64_t step0, uint64_t seed, int spc,
                                                                    int sweeps_between, int burn_in, int8_t *out_cfg,
@@ -793,8 +814,11 @@ void plan_weights(const Problem &p, TcPlan &pl) {
     pl.wbytes = 9u * p.C * p.C * 2u;
 }
 
-bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_bytes, TcPlan *out, std::string *why) {
+bool make_plan(const Problem &p, int G, int slots, int ctas, size_t max_smem, int extra_bytes, TcPlan *out,
+               std::string *why) {
     TcPlan pl{};
+    pl.ctas = ctas;
+    pl.epi = kMaxEpiWarps;
     pl.L = p.L;
     pl.Lp = p.L + 2;
     pl.N = p.N;
@@ -834,7 +858,8 @@ bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_by
     const uint32_t sm_bytes = 233472u;   // 228 KB per SM, 1 KB reserved per block
     while (cols * (sm_bytes / (o + 1024u)) > 512u) o += 1024u;
     pl.total = o;
-    if (cols > 512) { *why = "tensor-memory tiles do not fit in 512 columns"; return false; }
+    if (cols * (uint32_t)ctas > 512) { *why = "tensor-memory tiles do not fit in 512 columns"; return false; }
+    if ((uint32_t)ctas * (pl.total + 1024u) > sm_bytes) { *why = "shared memory plan exceeds the per-SM share"; return false; }
     if (pl.n_tiles > kMaxTiles) { *why = "more than 16 row tiles per group"; return false; }
     if (pl.rbuf >= (int)kNone) { *why = "row index range exceeds 16 bits"; return false; }
     if (pl.total > max_smem) { *why = "shared memory plan exceeds the per-block limit"; return false; }
@@ -845,7 +870,7 @@ bool make_plan(const Problem &p, int G, int slots, size_t max_smem, int extra_by
 int eloc_extra(const Problem &p) {
     const int chunk = bond_chunk(p);
     return (int)(al16(p.N) + al16(4 * chunk) + al16(8 * chunk) + al16(4 * (p.N + 1)) + sizeof(EnumScratch) +
-                 4 * sizeof(double) + 16 * (chunk + 1));
+                 4 * sizeof(double) + 16 * (chunk + 1) + 8 * 258);
 }
 
 int sample_extra(const Problem &p, int G, int slots) {
@@ -859,15 +884,32 @@ double plan_score(const Problem &p, const TcPlan &pl) {
     return (double)(p.N * pl.G) / (double)(pl.n_tiles * 128 + 4 * 128);
 }
 
-// NQS_TC_PLAN="G,slots" forces a plan (tuning); ignored if infeasible.
-bool forced_plan(int *G, int *slots) {
+// NQS_TC_PLAN="G,slots[,blocks per SM]" forces a plan (tuning); ignored if
+// infeasible or if the launch allows fewer blocks per SM.
+bool forced_plan(int *G, int *slots, int *ctas) {
     const char *s = getenv("NQS_TC_PLAN");
-    return s && sscanf(s, "%d,%d", G, slots) == 2 && *G >= 1 && *G <= 16 && *slots >= 1 && *slots <= kMaxSlots;
+    *ctas = 1;
+    if (!s) return false;
+    const int k = sscanf(s, "%d,%d,%d", G, slots, ctas);
+    return k >= 2 && *G >= 1 && *G <= 16 && *slots >= 1 && *slots <= kMaxSlots && *ctas >= 1 && *ctas <= 2;
 }
 
-bool best_plan(const Problem &p, size_t max_smem, bool eloc, int gmax, TcPlan *out, std::string *why) {
-    int fg, fs;
-    if (forced_plan(&fg, &fs) && make_plan(p, fg, fs, max_smem, eloc ? eloc_extra(p) : 0, out, why)) return true;
+bool best_plan(const Problem &p, size_t max_smem, bool eloc, int gmax, int max_ctas, TcPlan *out, std::string *why) {
+    int fg, fs, fc;
+    if (forced_plan(&fg, &fs, &fc) && fc <= max_ctas &&
+        make_plan(p, fg, fs, fc, max_smem, eloc ? eloc_extra(p) : 0, out, why))
+        return true;
+    // 16 channels: two co-resident blocks per SM with the largest group that
+    // fits, when that group has at least 3 configurations (measured on GB300,
+    // 6 layers: 1.32x at 10x10 J1-J2 with groups of 8, 1.13x at 12x12 t-J
+    // with groups of 3 over the one-block plan; slower with groups of 2, as
+    // at 16x16)
+    if (p.C == 16 && max_ctas >= 2) {
+        for (int G = gmax; G >= 3; --G) {
+            std::string w;
+            if (make_plan(p, G, 1, 2, max_smem, eloc ? eloc_extra(p) : 0, out, &w)) return true;
+        }
+    }
     // best one-slot plan; then two slots of the same G when they fit and a
     // slot has few tiles (measured on GB300: the epilogue tail after the last
     // MMA of a layer is then a large share of the layer, and the second slot
@@ -877,7 +919,7 @@ bool best_plan(const Problem &p, size_t max_smem, bool eloc, int gmax, TcPlan *o
     for (int G = 1; G <= gmax; ++G) {
         TcPlan pl;
         std::string w;
-        if (!make_plan(p, G, 1, max_smem, eloc ? eloc_extra(p) : 0, &pl, &w)) {
+        if (!make_plan(p, G, 1, 1, max_smem, eloc ? eloc_extra(p) : 0, &pl, &w)) {
             if (!found) *why = w;
             continue;
         }
@@ -887,7 +929,7 @@ bool best_plan(const Problem &p, size_t max_smem, bool eloc, int gmax, TcPlan *o
     if (found && out->n_tiles <= 8) {
         TcPlan two;
         std::string w;
-        if (make_plan(p, out->G, 2, max_smem, eloc ? eloc_extra(p) : 0, &two, &w)) *out = two;
+        if (make_plan(p, out->G, 2, 1, max_smem, eloc ? eloc_extra(p) : 0, &two, &w)) *out = two;
     }
     return found;
 }
@@ -943,16 +985,16 @@ int launch_logpsi_tc(const Problem &p, const double *, const void *packed, const
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
-    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, false, 16, &pl, &why)) {
+    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, false, 16, 2, &pl, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
     const int64_t per = pl.G * pl.slots;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, env.num_sms));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, (int64_t)env.num_sms * pl.ctas));
     NQS_TC_DISPATCH(p.C, {
         auto k = logpsi_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
-        k<<<grid, kTcThreads, pl.total, env.stream>>>(pl, (const unsigned char *)packed, configs, n, out, env.err);
+        k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, (const unsigned char *)packed, configs, n, out, env.err);
     });
     return check(env, "logpsi_tc_kernel");
 }
@@ -962,15 +1004,15 @@ int launch_eloc_tc(const Problem &p, const double *, const void *packed, const i
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
-    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, &pl, &why)) {
+    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, 2, &pl, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, env.num_sms));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * pl.ctas));
     NQS_TC_DISPATCH(p.C, {
         auto k = eloc_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
-        k<<<grid, kTcThreads, pl.total, env.stream>>>(pl, p, (const unsigned char *)packed, configs, logpsi, n, out,
+        k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, p, (const unsigned char *)packed, configs, logpsi, n, out,
                                                       env.err);
     });
     return check(env, "eloc_tc_kernel");
@@ -988,7 +1030,7 @@ int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, i
         const Problem &p = items[i].p;
         std::string why;
         TcPlan pl;
-        if (p.C != C || !tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, &pl, &why)) {
+        if (p.C != C || !tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, 1, &pl, &why)) {
             *env.msg = p.C != C ? std::string("grouped local energy needs one channel count per launch") : why;
             return NQS_ERR_UNSUPPORTED;
         }
@@ -1024,31 +1066,75 @@ int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, i
     return check(env, "eloc_tc_multi_kernel");
 }
 
+namespace {
+
+// Sampler plan: chains per block so that the blocks cover the SMs, one group
+// in flight (with one or two chains per block a second slot only adds fixed
+// per-forward costs). With at most two chains per SM, two co-resident blocks
+// of one chain each (measured on GB300: 1.3-1.4x faster than one block of two
+// chains, since a forward of one or two configurations is latency-bound and
+// the blocks overlap their layer boundaries).
+bool sample_plan(const Problem &p, int n_chains, size_t max_smem, int num_sms, TcPlan *out, std::string *why) {
+    int ctas = (n_chains + num_sms - 1) / num_sms <= 2 ? 2 : 1;
+    int fg = 0, fs = 0, fc = 1;
+    const char *force = getenv("NQS_TC_SAMPLE");   // "G,slots,blocks per SM" (tuning)
+    if (force && sscanf(force, "%d,%d,%d", &fg, &fs, &fc) == 3 && fc >= 1 && fc <= 2) ctas = fc;
+    for (; ctas >= 1; --ctas) {   // one block per SM if two do not fit
+        const int want = std::max(1, (n_chains + num_sms * ctas - 1) / (num_sms * ctas));
+        const int slots = fg > 0 ? std::min(std::max(fs, 1), kMaxSlots) : (want >= 8 ? 2 : 1);
+        for (int G = fg > 0 ? std::min(fg, 16) : std::min((want + slots - 1) / slots, 16); G >= 1; --G)
+            if (make_plan(p, G, slots, ctas, max_smem, sample_extra(p, G, slots), out, why)) return true;
+    }
+    return false;
+}
+
+}  // namespace
+
 int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_t *chains, int n_chains,
                      uint64_t step0, uint64_t seed, int spc, int sweeps_between, int burn_in, int8_t *out_cfg,
                      double *out_logpsi, const LaunchEnv &env) {
     std::string why;
-    if (!tc_supported(p, &why)) { *env.msg = why; return NQS_ERR_UNSUPPORTED; }
-    // chains per block: enough blocks to cover the SMs, one group in flight
-    // (measured: with one or two chains per block a second slot only adds
-    // fixed per-forward costs)
-    const int want = std::max(1, (n_chains + env.num_sms - 1) / env.num_sms);
-    const int slots = want >= 8 ? 2 : 1;
     TcPlan pl;
-    bool ok = false;
-    for (int G = std::min((want + slots - 1) / slots, 16); G >= 1 && !ok; --G)
-        ok = make_plan(p, G, slots, env.max_smem, sample_extra(p, G, slots), &pl, &why);
-    if (!ok) { *env.msg = why; return NQS_ERR_UNSUPPORTED; }
+    if (!tc_supported(p, &why) || !sample_plan(p, n_chains, env.max_smem, env.num_sms, &pl, &why)) {
+        *env.msg = why;
+        return NQS_ERR_UNSUPPORTED;
+    }
     const int per_block = pl.G * pl.slots;
     const int grid = (n_chains + per_block - 1) / per_block;
     NQS_TC_DISPATCH(p.C, {
         auto k = sample_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
-        k<<<grid, kTcThreads, pl.total, env.stream>>>(pl, (const unsigned char *)packed, chains, n_chains, per_block,
-                                                      step0, seed, spc, sweeps_between, burn_in, out_cfg, out_logpsi,
-                                                      env.err);
+        k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, (const unsigned char *)packed, chains,
+                                                                    n_chains, per_block, step0, seed, spc,
+                                                                    sweeps_between, burn_in, out_cfg, out_logpsi,
+                                                                    env.err);
     });
     return check(env, "sample_tc_kernel");
+}
+
+int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int num_sms, int32_t *out,
+                     std::string *why) {
+    TcPlan pl;
+    bool ok = tc_supported(p, why);
+    if (ok) {
+        if (kind == 2) ok = sample_plan(p, (int)n, max_smem, num_sms, &pl, why);
+        else ok = best_plan(p, max_smem, kind == 1, 16, 2, &pl, why);
+    }
+    if (!ok) return NQS_ERR_UNSUPPORTED;
+    const int64_t per = (int64_t)pl.G * pl.slots, cap = (int64_t)num_sms * pl.ctas;
+    int64_t grid;
+    if (kind == 2) grid = (n + per - 1) / per;
+    else if (kind == 1) grid = std::max<int64_t>(1, std::min<int64_t>(n, cap));
+    else grid = std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, cap));
+    out[0] = pl.G;
+    out[1] = pl.slots;
+    out[2] = pl.ctas;
+    out[3] = pl.epi;
+    out[4] = pl.n_tiles;
+    out[5] = (int32_t)pl.total;
+    out[6] = (int32_t)pl.tmem_cols;
+    out[7] = (int32_t)grid;
+    return NQS_OK;
 }
 
 }  // namespace nqs

@@ -131,6 +131,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Same load without the wait (several loads, then one tmem_wait_ld()).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ float tanh_approx(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -140,6 +151,13 @@ __device__ __forceinline__ float tanh_approx(float x) {
 // SiLU(z) = z * sigmoid(z) = 0.5 z (1 + tanh(z / 2)).
 __device__ __forceinline__ float silu_fast(float z) {
     const float hz = 0.5f * z;
+    return fmaf(hz, tanh_approx(hz), hz);
+}
+
+// SiLU(v + b) given hb = b / 2: 0.5 (v + b) is formed as fma(0.5, v, hb),
+// which rounds to the same value as 0.5f * (v + b) (scaling by 2 is exact).
+__device__ __forceinline__ float silu_bias(float v, float hb) {
+    const float hz = fmaf(0.5f, v, hb);
     return fmaf(hz, tanh_approx(hz), hz);
 }
 

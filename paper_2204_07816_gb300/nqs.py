@@ -19,13 +19,14 @@ NQS_OK = 0
 STATUS = {0: 'NQS_OK', -1: 'NQS_ERR_INVALID_ARG', -2: 'NQS_ERR_OOM', -3: 'NQS_ERR_CUDA', -4: 'NQS_ERR_NONFINITE',
           -5: 'NQS_ERR_NOT_CONVERGED', -6: 'NQS_ERR_TIMEOUT', -7: 'NQS_ERR_UNSUPPORTED'}
 NQS_ERR_NOT_CONVERGED = -5
+NQS_ERR_UNSUPPORTED = -7
 PRECISION = {'fp64': 0, 'fp32': 1, 'bf16': 2}
 MODEL = {'j1j2': 0, 'tj': 1}
 
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
-           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve')
+           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve', 'nqs_tc_plan')
 
 
 class nqs_problem(ctypes.Structure):
@@ -55,6 +56,7 @@ def load(path=LIB_PATH):
     P, I32, I64, U64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
     sig = {
         'nqs_param_count': (I64, [ctypes.POINTER(nqs_problem)]),
+        'nqs_tc_plan': (ctypes.c_int, [ctypes.POINTER(nqs_problem), I32, I64, I32, I32, ctypes.POINTER(I32)]),
         'nqs_init': (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(nqs_problem), P, U64, P]),
         'nqs_destroy': (ctypes.c_int, [P]),
         'nqs_last_error': (ctypes.c_char_p, [P]),
@@ -110,6 +112,25 @@ def make_problem(model='j1j2', L=4, J1=1.0, J2=0.5, t=1.0, J=0.4, n_up=None, n_d
 
 def nqs_param_count(problem):
     return load().nqs_param_count(ctypes.byref(problem))
+
+
+TC_PLAN_KIND = {'logpsi': 0, 'local_energy': 1, 'sample': 2}
+TC_PLAN_FIELDS = ('G', 'slots', 'blocks_per_sm', 'epilogue_warps', 'tiles', 'smem_bytes', 'tmem_cols', 'grid')
+
+
+def tc_plan(problem, kind, n, max_smem_per_block=232448, num_sms=152):
+    """nqs_tc_plan: the tensor-core plan the launchers choose (host only).
+    kind: 'logpsi', 'local_energy' (n = samples) or 'sample' (n = chains).
+    Returns a dict of TC_PLAN_FIELDS, or None if the tensor-core path cannot
+    run the problem."""
+    out = (ctypes.c_int32 * 8)()
+    rc = load().nqs_tc_plan(ctypes.byref(problem), TC_PLAN_KIND[kind], int(n), int(max_smem_per_block), int(num_sms),
+                            out)
+    if rc == NQS_ERR_UNSUPPORTED:
+        return None
+    if rc != 0:
+        raise NQSError(rc, 'nqs_tc_plan: invalid argument')
+    return dict(zip(TC_PLAN_FIELDS, list(out)))
 
 
 def local_energy_multi(contexts, configs, precision='bf16', outs=None, logpsi=None, max_blocks=0):
