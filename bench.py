@@ -134,6 +134,46 @@ def dense_forward_flops(w):
     return fl
 
 
+def cone_sites(L, l, nnn):
+    """Sites of layer l's output (l = 1 .. n_layers) that differ between a
+    configuration and one with two sites swapped: the union of the two
+    (2l+1)^2 squares around the swapped sites on the periodic L x L lattice
+    (exact while the squares do not wrap onto themselves, else all sites)."""
+    s = 2 * l + 1
+    if s + 1 > L:
+        return L * L
+    return 4 * l * l + 8 * l + 2 if nnn else s * (s + 1)
+
+
+def cone_forward_flops(w, nnn):
+    """FLOPs of the layers' outputs that change for one connected
+    configuration (the incremental forward)."""
+    fl = 0
+    for l in range(w['n_layers']):
+        cin = w['c_in'] if l == 0 else w['channels']
+        fl += 2 * 9 * cin * w['channels'] * cone_sites(w['L'], l + 1, nnn)
+    return fl
+
+
+def eloc_algorithmic_flops(w, n_samples, pairs, n_conn):
+    """(cone form, dense form) FLOPs of one E_loc launch: each sample's own
+    dense forward (it is recomputed) plus, per connected configuration, the
+    cone (incremental) or the full (dense) forward."""
+    L = w['L']
+    k = torch.arange(pairs.shape[1], device=pairs.device)[None, :] < n_conn[:, None].to(torch.int64)
+    i, j = pairs[..., 0].to(torch.int64), pairs[..., 1].to(torch.int64)
+    dx = (i % L - j % L).abs()
+    dy = (i // L - j // L).abs()
+    dx = torch.minimum(dx, L - dx)
+    dy = torch.minimum(dy, L - dy)
+    nnn = ((dx + dy) == 2) & k
+    n_nnn = int(nnn.sum().item())
+    n_nn = int(k.sum().item()) - n_nnn
+    dense = dense_forward_flops(w)
+    cone = n_samples * dense + n_nn * cone_forward_flops(w, False) + n_nnn * cone_forward_flops(w, True)
+    return float(cone), float((n_samples + n_nn + n_nnn) * dense)
+
+
 def load_peaks():
     path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
     if os.path.exists(path):
@@ -376,10 +416,13 @@ def main():
     value = job_throughput(n_samples * args.steps, world, eloc_total_ms)
     sr_steps_per_s = job_throughput(args.steps, world, step_total_ms)
 
-    # algorithmic FLOPs of one E_loc launch: (n_c + 1) dense forwards per sample
+    # algorithmic FLOPs of one E_loc launch: the sample's forward plus the
+    # changed cone of every connected configuration (the dense form, n_c + 1
+    # full forwards per sample, is reported beside it)
     cfg_last, e_last, _ = last
-    n_conn = ctx.connected(cfg_last)[0].to(torch.int64).sum().item()
-    flops = (n_conn + n_samples) * dense_forward_flops(w)
+    n_conn_s, pairs, _, _ = ctx.connected(cfg_last)
+    flops, flops_dense = eloc_algorithmic_flops(w, n_samples, pairs, n_conn_s)
+    del pairs
 
     # E_loc through the public API with host buffers (copies inside the timed region)
     cfg_host = cfg_last.cpu().pin_memory()
@@ -424,14 +467,20 @@ def main():
             peak = peaks.get('bf16_tflops_sustained') or peaks['bf16_tflops']
             roof = {'bound': 'tensor', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s',
                     'frac': achieved / peak, 'traffic': None, 'kernel': 'eloc_tc_kernel',
-                    'peak_source': '%s bf16 dense (sustained)' % peak_kind}
+                    'peak_source': '%s bf16 dense (sustained)' % peak_kind,
+                    'flops': 'cone form (changed sites only) %.4g per launch' % flops,
+                    'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,
+                                   'frac': flops_dense / eloc_launch_s / 1e12 / peak}}
         else:
             mhz = (clocks or {}).get('sm_mhz') or peaks.get('sm_max_mhz', 2070.0)
             lanes = 128 if args.precision == 'fp32' else 2
             peak = 152 * lanes * 2 * mhz * 1e6 / 1e12
             roof = {'bound': 'alu', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s', 'frac': achieved / peak,
                     'traffic': None, 'kernel': 'eloc_plain_kernel',
-                    'peak_source': '152 SMs x %d lanes x 2 FLOP x %.0f MHz' % (lanes, mhz)}
+                    'peak_source': '152 SMs x %d lanes x 2 FLOP x %.0f MHz' % (lanes, mhz),
+                    'flops': 'cone form (changed sites only) %.4g per launch' % flops,
+                    'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,
+                                   'frac': flops_dense / eloc_launch_s / 1e12 / peak}}
         # CPU oracle on a bounded sample of the same workload
         sub = cfg_last[:args.oracle_samples].cpu().numpy()
         e_or, dt_or = oracle_eloc(args.workload, params_at_step(ctx), sub, pool, cores)
