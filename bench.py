@@ -174,6 +174,36 @@ def eloc_algorithmic_flops(w, n_samples, pairs, n_conn):
     return float(cone), float((n_samples + n_nn + n_nnn) * dense)
 
 
+TRAFFIC_SOURCES = ('tc.cu', 'tc_ptx.cuh', 'common.cuh', 'internal.h')
+TRAFFIC_PROFILE = os.path.join(ROOT, 'profiles', 'eloc_tc_j1j2_10x10.md')
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, 'paper_2204_07816_gb300', 'csrc', name), 'rb') as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(n_samples):
+    """DRAM bytes (read + write) of one E_loc launch of n_samples, scaled
+    from the ncu capture recorded in the profile summary, or None if there is
+    no record or the kernel sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            for line in f:
+                if line.startswith('traffic-record:'):
+                    kv = dict(t.split('=', 1) for t in line.split(':', 1)[1].split())
+                    if kv.get('source_sha256') != kernel_source_hash():
+                        return None
+                    return float(kv['dram_bytes']) * n_samples / float(kv['samples'])
+    except (OSError, ValueError, KeyError):
+        return None
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
     if os.path.exists(path):
@@ -466,7 +496,7 @@ def main():
         if args.precision == 'bf16':
             peak = peaks.get('bf16_tflops_sustained') or peaks['bf16_tflops']
             roof = {'bound': 'tensor', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s',
-                    'frac': achieved / peak, 'traffic': None, 'kernel': 'eloc_tc_kernel',
+                    'frac': achieved / peak, 'traffic': recorded_traffic(n_samples), 'kernel': 'eloc_tc_kernel',
                     'peak_source': '%s bf16 dense (sustained)' % peak_kind,
                     'flops': 'cone form (changed sites only) %.4g per launch' % flops,
                     'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,

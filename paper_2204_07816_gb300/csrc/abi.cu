@@ -326,7 +326,12 @@ int nqs_local_energy(nqs_ctx *c, const int8_t *configs, const double *logpsi, in
     DeviceParams dp;
     if (int rc = prepare_params(c, prec, &dp)) return rc;
     LaunchEnv env = env_of(c);
-    if (prec == NQS_BF16) return launch_eloc_tc(c->p, c->params, c->packed, configs, logpsi, n, out, env);
+    if (prec == NQS_BF16) {
+        const size_t cb = tc_eloc_cache_bytes(c->p, c->max_smem, c->num_sms, n);
+        if (cb > 0)
+            if (int rc = ensure_scratch(c, cb)) return rc;
+        return launch_eloc_tc(c->p, c->params, c->packed, configs, logpsi, n, out, c->scratch, c->scratch_bytes, env);
+    }
     return launch_eloc_plain(c->p, prec, dp, configs, logpsi, n, out, env);
 }
 

@@ -56,8 +56,10 @@ size_t tc_packed_bytes(const Problem &p);
 int launch_tc_pack(const Problem &p, const double *p64, void *packed, const LaunchEnv &env);
 int launch_logpsi_tc(const Problem &p, const double *p64, const void *packed, const int8_t *configs, int64_t n,
                      double *out, const LaunchEnv &env);
+size_t tc_eloc_cache_bytes(const Problem &p, size_t max_smem, int num_sms, int64_t n);
 int launch_eloc_tc(const Problem &p, const double *p64, const void *packed, const int8_t *configs,
-                   const double *logpsi, int64_t n, double *out, const LaunchEnv &env);
+                   const double *logpsi, int64_t n, double *out, void *cache, size_t cache_bytes,
+                   const LaunchEnv &env);
 // grouped local energies of several problems with one channel count (tc.cu)
 struct TcMultiItem {
     Problem p;

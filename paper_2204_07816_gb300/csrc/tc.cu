@@ -96,6 +96,52 @@ struct TcState {        // per-CTA pipeline state (all threads keep identical co
     uint32_t wbase;     // first weight load of the bound problem (load q holds layer (q - wbase) mod n_layers)
 };
 
+// Rows a group computes, layer by layer: a connected configuration differs
+// from its sample in two sites, so layer l's output (0-based) differs from
+// the sample's own activations only within distance l + 1 of them (the cone
+// of Sec. 5.4.1's local energy). The two sites lie in one row (class 0) or
+// in adjacent rows (class 1); every configuration of a group shares the
+// class and is rolled along y so that its pair sits at canonical row `top`
+// (and top + 1). Layer l then computes canonical rows top - (l + 1) ...
+// top + cls + l + 1 only; rows outside that band hold the sample's own
+// activations, rolled by the same amount and copied in from a per-block
+// cache. The convolution is translation invariant with periodic padding, so
+// every value equals bitwise what the dense forward of the unrolled
+// configuration computes. cls < 0: dense (every row of every layer).
+struct Band {
+    int cls, top;
+    const int *roll;     // [G]: original row = (canonical row + roll[g]) mod L
+};
+
+__device__ __forceinline__ Band dense_band() { return Band{-1, 0, nullptr}; }
+
+// Band rows [lo, hi] of layer l; false if the layer is computed densely
+// (dense group, last layer, or the band spans the lattice).
+__device__ __forceinline__ bool band_rows(const TcPlan &pl, const Band &b, int l, int &lo, int &hi) {
+    if (b.cls < 0 || l >= pl.n_layers - 1) return false;
+    lo = b.top - (l + 1);
+    hi = b.top + b.cls + (l + 1);
+    return lo >= 0 && hi <= pl.L - 1 && hi - lo + 1 < pl.L;
+}
+
+// Tiles [t0, t1) holding layer l's rows.
+__device__ __forceinline__ void band_tiles(const TcPlan &pl, const Band &b, int l, int &t0, int &t1) {
+    int lo, hi;
+    t0 = 0;
+    t1 = pl.n_tiles;
+    if (!band_rows(pl, b, l, lo, hi)) return;
+    const int first = ((lo + 1) * pl.Lp + 1) * pl.G, last = ((hi + 1) * pl.Lp + pl.L) * pl.G + pl.G - 1;
+    t0 = (first - pl.r0) >> 7;
+    t1 = min(pl.n_tiles, ((last - pl.r0) >> 7) + 1);
+}
+
+// Per-block cache of the sample's activations, layers 0 .. n_layers - 2, in
+// padded positions: [layer][Lp * Lp][C / 8 planes][16 bytes].
+__host__ __device__ inline size_t sigma_cache_bytes(const TcPlan &pl) {
+    const size_t b = (size_t)(pl.n_layers - 1) * pl.Lp * pl.Lp * pl.C * 2;
+    return (b + 255) & ~(size_t)255;
+}
+
 // Barriers, TMEM address and abort flag sit at a fixed offset (0) so that a
 // block can re-bind to another problem without re-initialising them.
 constexpr uint32_t kBarBytes = 8 * (2 + kMaxSlots * kMaxTiles) + 16;
@@ -169,7 +215,7 @@ __device__ __forceinline__ void store_rows(const TcPlan &pl, uint32_t act, uint2
 // Spins of a slot to the padded lattice, then the layer-0 im2col matrix
 // (row = output row, K0 columns: tap-major, one-hot channel minor; zero
 // padded) into the slot's second activation buffer.
-__device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot) {
+__device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot, const Band &band) {
     const int G = pl.G;
     int8_t *spad = sh.spad + slot * pl.Lp * pl.Lp * G;
     const int8_t *spins = sh.spins + slot * G * pl.N;
@@ -188,7 +234,9 @@ __device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot) {
     for (int o = 0; o < 9; ++o) offg[o] = ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * G;
     const uint32_t a0 = act_addr(pl, sh, slot, 1);
     const uint32_t one = 0x3F80u, minus_one = 0xBF80u;   // bf16 +1, -1
-    for (int lr = threadIdx.x; lr < pl.n_tiles * 128; lr += blockDim.x) {
+    int t0, t1;
+    band_tiles(pl, band, 0, t0, t1);
+    for (int lr = t0 * 128 + (int)threadIdx.x; lr < t1 * 128; lr += blockDim.x) {
         const uint32_t main = sh.rowtab[lr].x & 0xFFFFu;
         const uint32_t row = (uint32_t)(pl.r0 + lr);
         uint32_t w[16];
@@ -219,7 +267,7 @@ __device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot) {
 // Issue the MMAs of layer l for one slot (issuer threads only).
 template <int C>
 __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int slot,
-                            int l, int *err) {
+                            int l, int *err, const Band &band) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = st.wseq + (uint32_t)l;
     const int iw = warp - pl.epi;   // issuer index
@@ -233,9 +281,11 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
             const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
             const uint64_t b_base = ptx::smem_desc(wb, C * 16, 128);
             const uint32_t idesc = ptx::idesc_bf16(128, C);
+            int t0, t1;
+            band_tiles(pl, band, l, t0, t1);
             if (l == 0) {
                 const uint64_t a_base = ptx::smem_desc(act_addr(pl, sh, slot, 1), pl.plane, 128);
-                for (int t = iw; t < pl.n_tiles; t += kIssuers) {
+                for (int t = t0 + iw; t < t1; t += kIssuers) {
                     const uint32_t arow = (uint32_t)(pl.r0 + t * 128);
                     for (int kk = 0; kk < pl.K0 / 16; ++kk)
                         ptx::mma_bf16(tmem + (uint32_t)(t * C), a_base + ((arow * 16u + (uint32_t)(2 * kk) * pl.plane) >> 4),
@@ -247,7 +297,7 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
                 uint32_t offs[9];
 #pragma unroll
                 for (int o = 0; o < 9; ++o) offs[o] = (uint32_t)(pl.r0 + ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * pl.G);
-                for (int t = iw; t < pl.n_tiles; t += kIssuers) {
+                for (int t = t0 + iw; t < t1; t += kIssuers) {
                     const uint32_t d = tmem + (uint32_t)(t * C);
 #pragma unroll
                     for (int o = 0; o < 9; ++o) {
@@ -273,7 +323,8 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
 // bias + SiLU, then bf16 rows (and halo images) or, after the last layer,
 // head contributions. Ends with a block barrier. False on abort.
 template <int C>
-__device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st, int slot, int l, int *err) {
+__device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st, int slot, int l, int *err,
+                               const Band &band, const unsigned char *cache, unsigned char *cache_w) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
     const bool last = l == pl.n_layers - 1;
     const uint32_t tmem = *sh.tmem_addr + (uint32_t)(slot * pl.slot_cols);
@@ -287,8 +338,48 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
     float hb[HB];
 #pragma unroll
     for (int c = 0; c < HB; ++c) hb[c] = 0.5f * bias[c];
+    int t0, t1, lo = 0, hi = 0;
+    band_tiles(pl, band, l, t0, t1);
+    const bool banded = band_rows(pl, band, l, lo, hi);
+    const uint32_t mlo = banded ? (uint32_t)((lo + 1) * pl.Lp * pl.G) : 0u;
+    const uint32_t mhi = banded ? (uint32_t)((hi + 2) * pl.Lp * pl.G) : kNone;
+    const int Lp2 = pl.Lp * pl.Lp;
+    constexpr int KC = C / 8;
+    if (banded && warp < pl.epi) {
+        // Rows the next layer reads that this layer does not compute: the
+        // sample's layer-l activations, rolled into each configuration's
+        // frame (with their periodic images), copied asynchronously from the
+        // cache while the tiles below are processed (waited for before the
+        // layer's closing barrier); disjoint from the band rows they write.
+        int nlo, nhi;
+        const bool next_banded = band_rows(pl, band, l + 1, nlo, nhi);
+        const int width = hi - lo + 1;
+        const int nf = next_banded ? 4 : pl.L - width;
+        const int items = pl.G * nf * pl.L;
+        for (int it = (int)threadIdx.x; it < items; it += 32 * pl.epi) {
+            const int q = it / pl.L, x = it - q * pl.L;
+            const int g = q / nf, f = q - g * nf;
+            int yc;
+            if (next_banded) yc = f < 2 ? lo - 2 + f : hi - 1 + f;   // lo - 2, lo - 1, hi + 1, hi + 2
+            else yc = f < lo ? f : f + width;
+            yc = (yc + pl.L) % pl.L;
+            int ys = yc + band.roll[g];
+            if (ys >= pl.L) ys -= pl.L;
+            const uint32_t src_pos = sh.sitetab[ys * pl.L + x].x & 0xFFFFu;
+            const unsigned char *src = cache + (size_t)(l * Lp2 + (int)src_pos) * KC * 16;
+            const uint2 d = sh.sitetab[yc * pl.L + x];
+            const uint32_t dp[4] = {d.x & 0xFFFFu, d.x >> 16, d.y & 0xFFFFu, d.y >> 16};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (dp[i] != kNone)
+#pragma unroll
+                    for (int kc = 0; kc < KC; ++kc)
+                        ptx::cp_async16(out + (uint32_t)kc * pl.plane + (dp[i] * (uint32_t)pl.G + (uint32_t)g) * 16u,
+                                        src + kc * 16);
+        }
+    }
     bool ok = true;
-    for (int t = warp >> 2; warp < pl.epi && t < pl.n_tiles; t += pl.epi / 4) {
+    for (int t = t0 + (warp >> 2); warp < pl.epi && t < t1; t += pl.epi / 4) {
         const uint32_t parity = (st.tphase >> (slot * kMaxTiles + t)) & 1u;
         const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
         const bool got = wait_or_abort(&sh.bar_tile[slot * kMaxTiles + t], parity, sh.abort_flag);
@@ -303,7 +394,7 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
 #pragma unroll
         for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
         const uint32_t main = dst.x & 0xFFFFu;
-        if (main == kNone) continue;
+        if (main == kNone || main < mlo || main >= mhi) continue;   // halo, or outside the band
         if (!last) {
             uint32_t w[C / 2];
 #pragma unroll
@@ -313,6 +404,14 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
                 w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
             }
             store_rows<C>(pl, out, dst, w);
+            if (cache_w) {   // the sample itself (configuration 0) fills the cache
+                const uint32_t pos = main / (uint32_t)pl.G;
+                if (main == pos * (uint32_t)pl.G) {
+                    uint4 *c4 = reinterpret_cast<uint4 *>(cache_w + (size_t)(l * Lp2 + (int)pos) * KC * 16);
+#pragma unroll
+                    for (int kc = 0; kc < KC; ++kc) c4[kc] = make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+                }
+            }
         } else {
             float ca = 0.f, cp = 0.f;
 #pragma unroll
@@ -326,7 +425,8 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
         }
     }
     if (!ok) raise_abort(sh, err);
-    st.tphase ^= ((1u << pl.n_tiles) - 1u) << (slot * kMaxTiles);
+    st.tphase ^= (((1u << (t1 - t0)) - 1u) << t0) << (slot * kMaxTiles);
+    if (banded) ptx::cp_async_wait_all();   // the fill's copies have landed
     ptx::tc_fence_before();
     ptx::fence_async_smem();
     __syncthreads();
@@ -334,15 +434,22 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
 }
 
 // a[g] = sum over sites of the head contributions (one warp per g, fixed order).
-__device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot) {
+__device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const int *roll) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G;
     const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act +
                                                            (uint32_t)(slot * 2 + ((pl.n_layers - 1) & 1)) * pl.act_bytes);
     double *res = sh.res + slot * 2 * G;
     for (int g = warp; g < G; g += (int)(blockDim.x >> 5)) {
         float sa = 0.f, sp = 0.f;
+        const int rg = roll ? roll[g] : 0;
         for (int site = lane; site < pl.N; site += 32) {
-            const int row = (int)(sh.sitetab[site].x & 0xFFFFu) * G + g;
+            // sum in the original site order, whatever frame the configuration was evaluated in
+            int cs = site;
+            if (rg) {
+                const int y = site / pl.L, x = site - y * pl.L;
+                cs = ((y - rg + pl.L) % pl.L) * pl.L + x;
+            }
+            const int row = (int)(sh.sitetab[cs].x & 0xFFFFu) * G + g;
             sa += contrib[2 * row];
             sp += contrib[2 * row + 1];
         }
@@ -361,17 +468,22 @@ __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot) {
 
 // Evaluate every slot's G configurations (sh.spins); results in sh.res.
 // Returns false if a wait timed out (the block must stop).
+// band: rows per layer (one slot only; dense_band() otherwise); cache: the
+// sample's activations (read by banded groups); cache_w: where a dense group
+// holding the sample as configuration 0 of slot 0 stores them (or null).
 template <int C>
-__device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int *err) {
+__device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int *err,
+                           const Band &band = dense_band(), const unsigned char *cache = nullptr,
+                           unsigned char *cache_w = nullptr) {
     for (int s = 0; s < pl.slots; ++s) {
-        build_slot(pl, sh, s);
-        issue_layer<C>(pl, sh, packed, st, s, 0, err);
+        build_slot(pl, sh, s, band);
+        issue_layer<C>(pl, sh, packed, st, s, 0, err, band);
     }
     for (int l = 0; l < pl.n_layers; ++l) {
         for (int s = 0; s < pl.slots; ++s) {
-            if (!epilogue_layer<C>(pl, sh, st, s, l, err)) return false;
-            if (l + 1 < pl.n_layers) issue_layer<C>(pl, sh, packed, st, s, l + 1, err);
-            else head_slot(pl, sh, s);
+            if (!epilogue_layer<C>(pl, sh, st, s, l, err, band, cache, s == 0 ? cache_w : nullptr)) return false;
+            if (l + 1 < pl.n_layers) issue_layer<C>(pl, sh, packed, st, s, l + 1, err, band);
+            else head_slot(pl, sh, s, band.roll);
         }
     }
     st.wseq += (uint32_t)pl.n_layers;
@@ -515,8 +627,8 @@ __global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) logpsi_tc_kernel(Tc
 template <int C>
 __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &sh, TcState &st,
                             const unsigned char *packed, const int8_t *cfg, const double *logpsi_s, double *out_s,
-                            int *err) {
-    const int G = pl.G, N = pl.N, per = G * pl.slots, chunk = bond_chunk(p);
+                            int *err, unsigned char *cache) {
+    const int G = pl.G, N = pl.N, L = pl.L, per = G * pl.slots, chunk = bond_chunk(p);
     unsigned char *ex = sh.base + pl.o_extra;
     int8_t *sigma = reinterpret_cast<int8_t *>(ex);
     int16_t *ci = reinterpret_cast<int16_t *>(ex + al16(N));
@@ -528,7 +640,12 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
     double *ref = reinterpret_cast<double *>(scr + 1);   // a0, phi0
     double *lp = ref + 4;                                 // [chunk + 1][2]: (a, phi) of every list entry
     double *fsum = lp + 2 * (chunk + 1);                  // [258] fixed-order sum scratch
+    int16_t *ord = reinterpret_cast<int16_t *>(fsum + 258);   // [chunk] evaluation order of the entries
+    int *roll = reinterpret_cast<int *>(ord + ((chunk + 1) & ~1));   // [32] per configuration of a group
     const int recompute = logpsi_s == nullptr;
+    // the cone of every connected configuration is evaluated alone when the
+    // sample itself is evaluated here (its activations fill the cache)
+    const bool cone = cache != nullptr && recompute && pl.slots == 1;
     for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = cfg[r];
     __syncthreads();
     if (p.model == NQS_MODEL_TJ) snake_prefix(p, sigma, cum, *scr);
@@ -543,26 +660,73 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
         hd_tot += hd;
         const int lead = (recompute && b0 == 0) ? 1 : 0;   // sigma itself evaluated first
         const int n_entries = nconn + lead;
+        // evaluation order: the first group (sigma and per - 1 entries) in list
+        // order; with cones, the other entries grouped by class (pair in one
+        // row, then pair in two rows), stable, so each group shares one band
+        const int first = cone ? min(nconn, per - lead) : nconn;
+        for (int k = threadIdx.x; k < first; k += blockDim.x) ord[k] = (int16_t)k;
+        int base0 = first, n0 = 0;
+        for (int cls = 0; cls < 2 && first < nconn; ++cls) {
+            int base = cls == 0 ? first : first + n0;
+            for (int k0 = first; k0 < nconn; k0 += blockDim.x) {
+                const int k = k0 + threadIdx.x;
+                int f = 0;
+                if (k < nconn) f = ((ci[k] / L) != (cj[k] / L)) == (cls == 1);
+                int tot;
+                const int off = block_exclusive_scan(f, scr->iscr, &tot);
+                if (f) ord[base + off] = (int16_t)k;
+                base += tot;
+            }
+            if (cls == 0) n0 = base - base0;
+        }
+        __syncthreads();
         for (int e0 = 0; e0 < n_entries; e0 += per) {
             const int cnt = min(per, n_entries - e0);
+            // band of this group: all entries of one class (never the group holding sigma)
+            Band band = dense_band();
+            if (cone && e0 >= lead + first) {
+                const int ka = ord[e0 - lead], kb = ord[e0 + cnt - 1 - lead];
+                const int ca = (ci[ka] / L) != (cj[ka] / L), cb = (ci[kb] / L) != (cj[kb] / L);
+                if (ca == cb) band = Band{ca, ca ? L / 2 - 1 : L / 2, roll};
+            }
+            if (threadIdx.x < per) {
+                int r = 0;
+                const int c = threadIdx.x;
+                if (band.cls >= 0 && c < cnt) {
+                    const int k = ord[e0 + c - lead];
+                    const int yi = ci[k] / L, yj = cj[k] / L;
+                    const int top = band.cls == 0 ? yi : ((yi + 1) % L == yj ? yi : yj);
+                    r = (top - band.top + L) % L;
+                }
+                roll[c] = r;
+            }
+            __syncthreads();
             for (int r = threadIdx.x; r < per * N; r += blockDim.x) {
                 const int c = r / N, site = r - c * N;
-                const int k = e0 + c - lead;
-                int v = sigma[site];
-                if (c < cnt && k >= 0) {
+                const int q = e0 + c - lead;   // list position (-1: sigma)
+                int v;
+                if (c >= cnt || q < 0) {
+                    v = sigma[site];
+                } else {
+                    const int k = ord[q];
+                    int s0 = site + roll[c] * L;   // original site: row + roll (mod L)
+                    if (s0 >= N) s0 -= N;
                     const int i = ci[k], j = cj[k];
-                    if (site == i) v = sigma[j];
-                    else if (site == j) v = sigma[i];
+                    v = sigma[s0 == i ? j : (s0 == j ? i : s0)];
                 }
                 sh.spins[r] = (int8_t)v;
             }
             __syncthreads();
-            if (!tc_forward<C>(pl, sh, packed, st, err)) return false;
+            if (!tc_forward<C>(pl, sh, packed, st, err, band, cache, (cone && lead && e0 == 0) ? cache : nullptr))
+                return false;
             if (threadIdx.x < cnt) {
                 const int c = threadIdx.x, sl = c / G, g = c - sl * G;
-                lp[2 * (e0 + c)] = sh.res[sl * 2 * G + g];
-                lp[2 * (e0 + c) + 1] = sh.res[sl * 2 * G + G + g];
+                const int q = e0 + c - lead;
+                const int idx = q < 0 ? 0 : ord[q] + lead;
+                lp[2 * idx] = sh.res[sl * 2 * G + g];
+                lp[2 * idx + 1] = sh.res[sl * 2 * G + G + g];
             }
+            __syncthreads();
         }
         __syncthreads();
         if (lead && threadIdx.x == 0) { ref[0] = lp[0]; ref[1] = lp[1]; }
@@ -588,16 +752,17 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
 }
 
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) eloc_tc_kernel(TcPlan pl, Problem p, const unsigned char *packed,
-                                                                 const int8_t *configs, const double *logpsi,
-                                                                 int64_t n, double *out, int *err) {
+__global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>)
+    eloc_tc_kernel(TcPlan pl, Problem p, const unsigned char *packed, const int8_t *configs, const double *logpsi,
+                   int64_t n, double *out, int *err, unsigned char *cache) {
     extern __shared__ __align__(128) unsigned char smem[];
     TcShared sh;
     TcState st;
     tc_setup(pl, sh, smem, packed, st);
+    unsigned char *my_cache = cache ? cache + (size_t)blockIdx.x * sigma_cache_bytes(pl) : nullptr;
     for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
         if (!eloc_sample<C>(pl, p, sh, st, packed, configs + s * p.N, logpsi ? logpsi + 2 * s : nullptr, out + 2 * s,
-                            err))
+                            err, my_cache))
             break;
     tc_teardown(pl, sh, st);
 }
@@ -645,7 +810,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eloc_tc_multi_kernel(const TcRe
         }
         const int64_t s = g - reqs[r].start;
         const double *lps = reqs[r].logpsi ? reqs[r].logpsi + 2 * s : nullptr;
-        if (!eloc_sample<C>(pl, p, sh, st, reqs[r].packed, reqs[r].configs + s * p.N, lps, reqs[r].out + 2 * s, err))
+        if (!eloc_sample<C>(pl, p, sh, st, reqs[r].packed, reqs[r].configs + s * p.N, lps, reqs[r].out + 2 * s, err,
+                            nullptr))
             break;
     }
     tc_fini(sh, st, tmem_cols);
@@ -870,7 +1036,7 @@ bool make_plan(const Problem &p, int G, int slots, int ctas, size_t max_smem, in
 int eloc_extra(const Problem &p) {
     const int chunk = bond_chunk(p);
     return (int)(al16(p.N) + al16(4 * chunk) + al16(8 * chunk) + al16(4 * (p.N + 1)) + sizeof(EnumScratch) +
-                 4 * sizeof(double) + 16 * (chunk + 1) + 8 * 258);
+                 4 * sizeof(double) + 16 * (chunk + 1) + 8 * 258 + 2 * ((chunk + 1) & ~1) + 4 * 32);
 }
 
 int sample_extra(const Problem &p, int G, int slots) {
@@ -999,8 +1165,29 @@ int launch_logpsi_tc(const Problem &p, const double *, const void *packed, const
     return check(env, "logpsi_tc_kernel");
 }
 
+// Bytes of the per-block cache of sample activations the E_loc launch
+// uses to evaluate connected configurations on their cones only (0: the
+// plan evaluates them densely). Cones are used with one-block-per-SM plans:
+// measured on GB300 (E_loc, cones vs dense) 1.06x t-J 12x12 (32 channels),
+// 1.12x 16x16 (32 channels), 1.13x 16x16 (16 channels), 1.25x 24x24; with
+// two blocks per SM (10x10, 8x8, t-J 12x12 with 16 channels) the fixed
+// per-layer costs of a band (the fill, a shorter tile pipeline) outweigh
+// the saved tiles (0.93-0.98x). NQS_TC_DENSE=1 turns the cones off,
+// NQS_TC_CONES=1 forces them wherever a plan allows (tuning).
+size_t tc_eloc_cache_bytes(const Problem &p, size_t max_smem, int num_sms, int64_t n) {
+    std::string why;
+    TcPlan pl;
+    if (n <= 0 || !tc_supported(p, &why) || !best_plan(p, max_smem, true, 16, 2, &pl, &why)) return 0;
+    const char *d = getenv("NQS_TC_DENSE"), *f = getenv("NQS_TC_CONES");
+    const bool force = f && f[0] == '1';
+    if (pl.slots != 1 || p.n_layers < 2 || (d && d[0] == '1') || (pl.ctas != 1 && !force)) return 0;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * pl.ctas));
+    return (size_t)grid * sigma_cache_bytes(pl);
+}
+
 int launch_eloc_tc(const Problem &p, const double *, const void *packed, const int8_t *configs,
-                   const double *logpsi, int64_t n, double *out, const LaunchEnv &env) {
+                   const double *logpsi, int64_t n, double *out, void *cache, size_t cache_bytes,
+                   const LaunchEnv &env) {
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
@@ -1009,11 +1196,13 @@ int launch_eloc_tc(const Problem &p, const double *, const void *packed, const i
         return NQS_ERR_UNSUPPORTED;
     }
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * pl.ctas));
+    const size_t need = tc_eloc_cache_bytes(p, env.max_smem, env.num_sms, n);
+    unsigned char *c = (need > 0 && cache && cache_bytes >= need) ? (unsigned char *)cache : nullptr;
     NQS_TC_DISPATCH(p.C, {
         auto k = eloc_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
-        k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, p, (const unsigned char *)packed, configs, logpsi, n, out,
-                                                      env.err);
+        k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, p, (const unsigned char *)packed, configs,
+                                                                    logpsi, n, out, env.err, c);
     });
     return check(env, "eloc_tc_kernel");
 }

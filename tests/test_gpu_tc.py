@@ -89,6 +89,36 @@ def test_local_energy_bf16_deterministic_across_batches():
     assert torch.equal(e1[10:20], e2)
 
 
+CONE_CASES = TC_CASES + [
+    ('j1j2_10x10', {'L': 7, 'n_up': 25, 'n_down': 24, 'n_layers': 5}),
+    ('tj_12x12', {'channels': 16}),
+    ('j1j2_10x10', {'L': 24, 'n_up': 288, 'n_down': 288, 'n_layers': 6}),
+]
+
+
+@pytest.mark.parametrize('case', CONE_CASES, ids=_ids)
+def test_local_energy_bf16_cones_equal_dense(case, monkeypatch):
+    """Connected configurations evaluated on their cones only (rolled into a
+    common frame, rows outside the cone copied from the sample's own
+    activations) give bitwise the local energies of the dense forward, and
+    the sample's supplied-log-psi path (dense) agrees to rounding."""
+    name, over = case
+    w = WL[name]
+    ctx, _ = make_ctx(w, **over)
+    n = 24 if over.get('L', w['L']) >= 24 else 48
+    cfg = dev(configs_for(w, n, seed=31, **over))
+    monkeypatch.setenv('NQS_TC_CONES', '1')     # also where the plan would not use them by default
+    cone = ctx.local_energy(cfg, None, 'bf16')
+    monkeypatch.delenv('NQS_TC_CONES')
+    monkeypatch.setenv('NQS_TC_DENSE', '1')
+    dense = ctx.local_energy(cfg, None, 'bf16')
+    monkeypatch.delenv('NQS_TC_DENSE')
+    torch.cuda.synchronize()
+    assert torch.equal(cone, dense)
+    again = ctx.local_energy(cfg, None, 'bf16')     # default plan choice
+    assert torch.equal(again, cone)
+
+
 def test_local_energy_bf16_zero_network():
     w = WL['j1j2_10x10']
     from tests.gpu_common import problem_of
