@@ -159,6 +159,7 @@ def eloc_algorithmic_flops(w, n_samples, pairs, n_conn):
     """(cone form, dense form) FLOPs of one E_loc launch: each sample's own
     dense forward (it is recomputed) plus, per connected configuration, the
     cone (incremental) or the full (dense) forward."""
+    import torch
     L = w['L']
     k = torch.arange(pairs.shape[1], device=pairs.device)[None, :] < n_conn[:, None].to(torch.int64)
     i, j = pairs[..., 0].to(torch.int64), pairs[..., 1].to(torch.int64)
