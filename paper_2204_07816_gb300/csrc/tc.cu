@@ -1272,7 +1272,12 @@ bool sample_plan(const Problem &p, int n_chains, size_t max_smem, int num_sms, T
         const int want = std::max(1, (n_chains + num_sms * ctas - 1) / (num_sms * ctas));
         const int slots = fg > 0 ? std::min(std::max(fs, 1), kMaxSlots) : (want >= 8 ? 2 : 1);
         for (int G = fg > 0 ? std::min(fg, 16) : std::min((want + slots - 1) / slots, 16); G >= 1; --G)
-            if (make_plan(p, G, slots, ctas, max_smem, sample_extra(p, G, slots), out, why)) return true;
+            if (make_plan(p, G, slots, ctas, max_smem, sample_extra(p, G, slots), out, why)) {
+                // a sampler group is one or a few tiles: one epilogue warp per
+                // TMEM lane quarter (measured 8 % faster than eight warps)
+                if (out->slots * out->n_tiles <= 4) out->epi = 4;
+                return true;
+            }
     }
     return false;
 }
