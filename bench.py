@@ -46,6 +46,8 @@ def parse():
                     help='profiling mode: only run --steps E_loc passes over S uniform random samples')
     ap.add_argument('--serve', type=int, default=0, metavar='R',
                     help='serving mode: R Poisson-arriving SR-step requests of mixed lattices (continuous batching)')
+    ap.add_argument('--serve-partition', action='store_true',
+                    help='serving mode with per-class SM shares (default: every request sized for the whole GPU)')
     return ap.parse_args()
 
 
@@ -85,8 +87,9 @@ def run_serve(args):
     from paper_2204_07816_gb300.serving import Server
     nbuild.build()
     reqs = serve_mix(args.serve)
-    server = Server(device='cuda', precision='bf16')
+    server = Server(device='cuda', precision='bf16', partition_sms=args.serve_partition)
     results, summary = server.run(reqs)
+    summary['sm_partition'] = bool(args.serve_partition)
     per = [{'rid': r.rid, 'model': r.model, 'L': r.L, 'channels': r.channels, 'n_layers': r.n_layers,
             'samples': r.n_samples, 'arrival_s': round(r.arrival, 3),
             'step_ms': [round(x * 1e3, 1) for x in results[r.rid].latencies],

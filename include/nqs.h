@@ -124,6 +124,23 @@ const char *nqs_last_error(const nqs_ctx *ctx);
 /* Wait for the context's stream; return and clear the latched device error. */
 int nqs_sync(nqs_ctx *ctx);
 
+/* Size every later launch of this context for `sms` SMs instead of the
+ * whole device (0 = whole device, the default; 1 .. SM count), so that
+ * contexts running side by side on their own streams (a serving mix) keep
+ * to disjoint shares of the GPU: grid sizes, chains per sampler block and
+ * the E_loc cache follow the limit. Host only; NQS_ERR_INVALID_ARG if sms
+ * is out of range. */
+int nqs_set_sm_limit(nqs_ctx *ctx, int32_t sms);
+
+/* Failure-path check of the device-side waits. Enqueues on the context's
+ * stream a one-warp kernel that waits, through the same bounded wait loop
+ * as the tensor-core kernels (limited here to `iterations` polls), on an
+ * mbarrier phase that nothing completes. When the limit runs out the kernel
+ * sets the timeout bit and exits; the next nqs_sync returns
+ * NQS_ERR_TIMEOUT and clears it, and the context stays usable. No GPU fault
+ * or hang is involved. iterations: 1 .. 1e6 (else NQS_ERR_INVALID_ARG). */
+int nqs_probe_wait_timeout(nqs_ctx *ctx, int64_t iterations);
+
 /* Number of GPU kernels this context has launched so far (a monotone
  * counter for accounting; -1 if ctx is NULL). Host only. */
 int64_t nqs_kernel_launches(const nqs_ctx *ctx);

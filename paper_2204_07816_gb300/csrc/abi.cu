@@ -18,6 +18,7 @@ struct nqs_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
+    int sm_limit = 0;              // 0: whole device; else grids are sized for this many SMs
     size_t max_smem = 0;
     int *err_dev = nullptr;        // device error bits
     float *params32 = nullptr;     // float copy for the FP32 path
@@ -82,10 +83,12 @@ Problem make_problem(const nqs_problem *q) {
     return p;
 }
 
+int sms_of(const nqs_ctx *c) { return (c->sm_limit > 0 && c->sm_limit < c->num_sms) ? c->sm_limit : c->num_sms; }
+
 LaunchEnv env_of(nqs_ctx *c) {
     LaunchEnv e;
     e.stream = c->stream;
-    e.num_sms = c->num_sms;
+    e.num_sms = sms_of(c);
     e.max_smem = c->max_smem;
     e.err = c->err_dev;
     e.launches = &c->launches;
@@ -208,6 +211,20 @@ int nqs_sync(nqs_ctx *c) {
     return NQS_OK;
 }
 
+int nqs_set_sm_limit(nqs_ctx *c, int32_t sms) {
+    if (!c) return NQS_ERR_INVALID_ARG;
+    if (sms < 0 || sms > c->num_sms) return fail(c, NQS_ERR_INVALID_ARG, "nqs_set_sm_limit: bad SM count");
+    c->sm_limit = sms;
+    return NQS_OK;
+}
+
+int nqs_probe_wait_timeout(nqs_ctx *c, int64_t iterations) {
+    if (int rc = check_ctx(c)) return rc;
+    if (iterations < 1 || iterations > 1000000) return fail(c, NQS_ERR_INVALID_ARG, "nqs_probe_wait_timeout: bad count");
+    LaunchEnv env = env_of(c);
+    return launch_wait_probe(iterations, env);
+}
+
 int nqs_destroy(nqs_ctx *c) {
     if (!c) return NQS_ERR_INVALID_ARG;
     int rc = nqs_sync(c);
@@ -327,7 +344,7 @@ int nqs_local_energy(nqs_ctx *c, const int8_t *configs, const double *logpsi, in
     if (int rc = prepare_params(c, prec, &dp)) return rc;
     LaunchEnv env = env_of(c);
     if (prec == NQS_BF16) {
-        const size_t cb = tc_eloc_cache_bytes(c->p, c->max_smem, c->num_sms, n);
+        const size_t cb = tc_eloc_cache_bytes(c->p, c->max_smem, sms_of(c), n);
         if (cb > 0)
             if (int rc = ensure_scratch(c, cb)) return rc;
         return launch_eloc_tc(c->p, c->params, c->packed, configs, logpsi, n, out, c->scratch, c->scratch_bytes, env);
@@ -408,12 +425,12 @@ int nqs_logpsi_grad(nqs_ctx *c, const int8_t *configs, int64_t n, double *O, int
     DeviceParams dp;
     if (int rc = prepare_params(c, gp, &dp)) return rc;
     if (gp == NQS_FP32 && grad_fast_supported(c->p, c->max_smem)) {
-        const int fb = (int)std::min<int64_t>(n, (int64_t)c->num_sms * grad_fast_blocks_per_sm(c->p));
+        const int fb = (int)std::min<int64_t>(n, (int64_t)sms_of(c) * grad_fast_blocks_per_sm(c->p));
         if (int rc = ensure_scratch(c, grad_fast_scratch_bytes(c->p, fb))) return rc;
         LaunchEnv env = env_of(c);
         return launch_grad_fast(c->p, c->params32, c->params, configs, n, O, c->scratch, c->scratch_bytes, env);
     }
-    const int blocks = (int)std::min<int64_t>(n, (int64_t)c->num_sms * 2);
+    const int blocks = (int)std::min<int64_t>(n, (int64_t)sms_of(c) * 2);
     if (int rc = ensure_scratch(c, grad_scratch_bytes(c->p, gp, blocks))) return rc;
     LaunchEnv env = env_of(c);
     return launch_grad_plain(c->p, gp, dp, configs, n, O, c->scratch, c->scratch_bytes, env);
@@ -427,6 +444,10 @@ int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, dou
     if (!(eps >= 0.0) || !(rtol >= 0.0) || max_iter < 0) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve: bad eps/rtol/max_iter");
     if (int rc = ensure_scratch(c, sr_workspace_doubles(n, c->p.P) * sizeof(double))) return rc;
     LaunchEnv env = env_of(c);
+    // the CG's partial sums are split by the device's SM count, not by an SM
+    // limit, so the solve's rounding does not depend on the share a context
+    // holds (its kernels are short; they do not pin SMs)
+    env.num_sms = c->num_sms;
     int iters = 0;
     double resid = 0.0, energy[2] = {0.0, 0.0};
     const int rc = run_sr_solve(c->p, O, eloc, n, eps, rtol, max_iter, lr, delta, c->params, apply_update,

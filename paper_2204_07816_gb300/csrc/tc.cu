@@ -167,8 +167,9 @@ __device__ __forceinline__ void issue_weight_load(const TcPlan &pl, const TcShar
 
 // Wait on an mbarrier phase; gives up when another thread raised the abort
 // flag or after the iteration limit.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, const int *abort_flag) {
-    for (long long it = 0; it < ptx::kWaitLimit; ++it) {
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, const int *abort_flag,
+                                              long long limit = ptx::kWaitLimit) {
+    for (long long it = 0; it < limit; ++it) {
         if (ptx::mbar_try_wait(bar, parity)) return true;
         if ((it & 255) == 255 && *(volatile const int *)abort_flag) return false;
     }
@@ -593,6 +594,22 @@ __device__ void tc_setup(const TcPlan &pl, TcShared &sh, unsigned char *smem, co
 __device__ void tc_teardown(const TcPlan &pl, TcShared &sh, TcState &st) { tc_fini(sh, st, pl.tmem_cols); }
 
 // ---------------------------------------------------------------- kernels
+// Failure-path check: one warp waits, through the kernels' bounded wait, on
+// an mbarrier phase that nothing completes; when the limit runs out it sets
+// the timeout bit exactly as a stalled pipeline would, and exits.
+__global__ void wait_probe_kernel(int *err, long long limit) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool got = wait_or_abort(&bar, 0, &abort_flag, limit);
+    if (!__all_sync(0xffffffffu, got) && threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+}
+
 template <int C>
 __global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) logpsi_tc_kernel(TcPlan pl, const unsigned char *packed,
                                                                    const int8_t *configs, int64_t n, double *out,
@@ -845,10 +862,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     double *pu = reinterpret_cast<double *>(ex + al16(per_block * N) + al16(4 * (2 * per_block + S * (G + 1))));
     double *ca = pu + per_block;
     double *cphi = ca + per_block;
-    const int c0 = blockIdx.x * per_block;
+    // chain groups: group k = blockIdx.x + j * gridDim.x (one pass when the
+    // grid covers every group; fewer blocks when the launch is held to an SM share)
+    bool ok = true;
+    for (int c0 = blockIdx.x * per_block; ok && c0 < n_chains; c0 += gridDim.x * per_block) {
     const int gc = min(per_block, n_chains - c0);
-    bool ok = gc > 0;
-    if (ok) {
+    {
         for (int r = threadIdx.x; r < gc * N; r += blockDim.x) cur[r] = chains[(size_t)c0 * N + r];
         __syncthreads();
         for (int r = threadIdx.x; r < per_block * N; r += blockDim.x) {
@@ -931,8 +950,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
             __syncthreads();
         }
     }
-    if (gc > 0 && ok)
+    if (ok)
         for (int r = threadIdx.x; r < gc * N; r += blockDim.x) chains[(size_t)c0 * N + r] = cur[r];
+    __syncthreads();
+    }
     tc_teardown(pl, sh, st);
 }
 
@@ -1294,7 +1315,7 @@ int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_
         return NQS_ERR_UNSUPPORTED;
     }
     const int per_block = pl.G * pl.slots;
-    const int grid = (n_chains + per_block - 1) / per_block;
+    const int grid = std::min((n_chains + per_block - 1) / per_block, env.num_sms * pl.ctas);
     NQS_TC_DISPATCH(p.C, {
         auto k = sample_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
@@ -1304,6 +1325,11 @@ int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_
                                                                     env.err);
     });
     return check(env, "sample_tc_kernel");
+}
+
+int launch_wait_probe(int64_t iterations, const LaunchEnv &env) {
+    wait_probe_kernel<<<1, 32, 0, env.stream>>>(env.err, (long long)iterations);
+    return check(env, "wait_probe_kernel");
 }
 
 int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int num_sms, int32_t *out,
@@ -1317,7 +1343,7 @@ int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int
     if (!ok) return NQS_ERR_UNSUPPORTED;
     const int64_t per = (int64_t)pl.G * pl.slots, cap = (int64_t)num_sms * pl.ctas;
     int64_t grid;
-    if (kind == 2) grid = (n + per - 1) / per;
+    if (kind == 2) grid = std::min<int64_t>((n + per - 1) / per, cap);
     else if (kind == 1) grid = std::max<int64_t>(1, std::min<int64_t>(n, cap));
     else grid = std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, cap));
     out[0] = pl.G;

@@ -26,7 +26,7 @@ MODEL = {'j1j2': 0, 'tj': 1}
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
-           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve', 'nqs_tc_plan')
+           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_set_sm_limit')
 
 
 class nqs_problem(ctypes.Structure):
@@ -62,6 +62,8 @@ def load(path=LIB_PATH):
         'nqs_last_error': (ctypes.c_char_p, [P]),
         'nqs_sync': (ctypes.c_int, [P]),
         'nqs_kernel_launches': (I64, [P]),
+        'nqs_probe_wait_timeout': (ctypes.c_int, [P, I64]),
+        'nqs_set_sm_limit': (ctypes.c_int, [P, I32]),
         'nqs_logpsi': (ctypes.c_int, [P, P, I64, P, I32]),
         'nqs_connected': (ctypes.c_int, [P, P, I64, I32, P, P, P, P]),
         'nqs_local_energy': (ctypes.c_int, [P, P, P, I64, P, I32]),
@@ -264,6 +266,15 @@ class Context:
                                         _ptr(cfg, torch.int8, 'configs_out'), _ptr(lp, torch.float64, 'logpsi_out'),
                                         _prec(precision)))
         return cfg, lp
+
+    def set_sm_limit(self, sms):
+        """nqs_set_sm_limit: size later launches for `sms` SMs (0 = all)."""
+        self._check(self.lib.nqs_set_sm_limit(self.ctx, int(sms)))
+
+    def probe_wait_timeout(self, iterations=1000):
+        """nqs_probe_wait_timeout: a bounded device wait that runs out; the
+        next sync() raises NQSError with NQS_ERR_TIMEOUT."""
+        self._check(self.lib.nqs_probe_wait_timeout(self.ctx, int(iterations)))
 
     def get_chains(self, n_chains):
         out = torch.empty((n_chains, self.N), dtype=torch.int8, device=self.device)

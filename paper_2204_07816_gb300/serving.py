@@ -18,7 +18,19 @@ runs its own loop of SR steps in a host thread:
   3. local derivatives and the SR solve on its stream.
 
 A request that arrives while others run is admitted as soon as memory is
-returned by a finished one and joins the next grouped launch. Every kernel
+returned by a finished one and joins the next grouped launch.
+
+Optional SM shares (`partition_sms=True`, `_Partition`): while requests of
+both size classes run, the large class (lattices above 16 x 16) is held to
+`large_frac` of the SMs and the small class keeps the rest; within a class
+the budget is split evenly (at least 4 SMs a request), and a class running
+alone gets the whole GPU. Every launch of a request is then sized for its
+share (nqs_set_sm_limit; results do not change), and the grouped E_loc
+launches of a class are capped at the class budget. On the measured mix
+(up to 36 x 36) the shares made every step slower (p50 5.1 s against 1.9 s
+shared): the large requests' sampler and backward, held to fewer blocks,
+keep their SMs proportionally longer, and the hardware scheduler already
+interleaves the streams; sharing the whole GPU is the default. Every kernel
 reduces in a fixed order and per-configuration results do not depend on
 what else shares a launch, so a request's trajectory is the same alone and
 in any mix. Step latency = from the start of a request's step (sampling) to
@@ -104,6 +116,50 @@ def footprint_bytes(req):
     return params + chains + samples + O + max(sr, grad) + (4 << 20)
 
 
+class _Partition:
+    """SM budgets of the running requests (see the module notes)."""
+
+    SMALL_SITES = 256
+
+    def __init__(self, num_sms, large_frac=0.5, min_sms=4):
+        self.num_sms = num_sms
+        self.large_frac = large_frac
+        self.min_sms = min_sms
+        self.lock = threading.Lock()
+        self.large = {}      # rid -> True for the large class
+
+    @classmethod
+    def is_large(cls, req):
+        return req.L * req.L > cls.SMALL_SITES
+
+    def add(self, req):
+        with self.lock:
+            self.large[req.rid] = self.is_large(req)
+
+    def remove(self, rid):
+        with self.lock:
+            self.large.pop(rid, None)
+
+    def class_budget(self, large):
+        """SMs of a class; 0 if the class may use the whole GPU."""
+        with self.lock:
+            n_large = sum(1 for v in self.large.values() if v)
+            n_small = len(self.large) - n_large
+        if n_large == 0 or n_small == 0:
+            return 0
+        b_large = max(self.min_sms, int(round(self.num_sms * self.large_frac)))
+        return b_large if large else self.num_sms - b_large
+
+    def limit(self, rid):
+        """SMs one request's launches are sized for (0 = whole GPU)."""
+        with self.lock:
+            large = self.large.get(rid, False)
+            n_class = sum(1 for v in self.large.values() if v == large)
+        budget = self.class_budget(large) or self.num_sms
+        share = max(self.min_sms, budget // max(1, n_class))
+        return 0 if share >= self.num_sms else share
+
+
 class _Run:
     def __init__(self, req, device, precision, sr_args):
         self.req = req
@@ -127,11 +183,13 @@ class _Run:
         self.cfg = None
         self.error = None
 
-    def loop(self, batcher, t0, on_done):
+    def loop(self, batcher, t0, on_done, partition=None):
         try:
             torch.cuda.set_device(self.device)
             for step in range(self.req.n_steps):
                 start = time.perf_counter()
+                if partition is not None:
+                    self.ctx.set_sm_limit(partition.limit(self.req.rid))
                 with torch.cuda.stream(self.stream):
                     self.cfg, _ = self.ctx.sample(self.req.n_chains, self.spc, 1,
                                                   self.req.burn_in if step == 0 else 0, self.precision)
@@ -166,8 +224,9 @@ class _Batcher:
 
     SMALL_SITES = 256
 
-    def __init__(self, device, precision, num_sms, window_s=0.0005):
+    def __init__(self, device, precision, num_sms, window_s=0.0005, partition=None):
         self.q = queue.Queue()
+        self.partition = partition
         self.device = device
         self.precision = precision
         self.num_sms = num_sms
@@ -200,9 +259,15 @@ class _Batcher:
                 key = (r.req.L * r.req.L > self.SMALL_SITES, r.req.channels)
                 classes.setdefault(key, []).append(r)
             total = sum(r.req.eloc_cost() for r in batch)
-            for group in classes.values():
-                share = sum(r.req.eloc_cost() for r in group) / total
-                blocks = max(8, int(round(self.num_sms * share))) if len(classes) > 1 else 0
+            for key, group in classes.items():
+                if self.partition is not None:
+                    # the class budget, split among the channel groups of that class in this batch
+                    budget = self.partition.class_budget(key[0])
+                    n_groups = sum(1 for k in classes if k[0] == key[0])
+                    blocks = max(8, budget // n_groups) if budget else (self.num_sms // n_groups if n_groups > 1 else 0)
+                else:
+                    share = sum(r.req.eloc_cost() for r in group) / total
+                    blocks = max(8, int(round(self.num_sms * share))) if len(classes) > 1 else 0
                 lead = group[0]
                 try:
                     for r in group:
@@ -225,7 +290,7 @@ class _Batcher:
 
 class Server:
     def __init__(self, device='cuda', hbm_budget_bytes=None, precision='bf16', eps=1e-4, rtol=1e-8,
-                 max_iter=10000, lr=0.02):
+                 max_iter=10000, lr=0.02, partition_sms=False, large_frac=0.5):
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device('cuda', torch.cuda.current_device())
@@ -235,6 +300,8 @@ class Server:
         self.budget = hbm_budget_bytes
         self.precision = precision
         self.sr_args = dict(eps=eps, rtol=rtol, max_iter=max_iter, lr=lr)
+        self.partition_sms = partition_sms
+        self.large_frac = large_frac
         self.events = []          # (time, kind, rid) log: 'admit', 'retire'
 
     def run(self, requests):
@@ -243,7 +310,8 @@ class Server:
             if footprint_bytes(r) > self.budget:
                 raise ValueError('request %d needs more memory than the whole budget' % r.rid)
         num_sms = torch.cuda.get_device_properties(self.device).multi_processor_count
-        batcher = _Batcher(self.device, self.precision, num_sms)
+        partition = _Partition(num_sms, self.large_frac) if self.partition_sms else None
+        batcher = _Batcher(self.device, self.precision, num_sms, partition=partition)
         lock = threading.Lock()
         finished = []
         results = {}
@@ -265,6 +333,8 @@ class Server:
                     if run.error:
                         raise run.error
                     results[run.req.rid] = run.result
+                    if partition is not None:
+                        partition.remove(run.req.rid)
                     used -= footprint_bytes(run.req)
                     run.close()
                     self.events.append((time.perf_counter() - t0, 'retire', run.req.rid))
@@ -274,7 +344,9 @@ class Server:
                     run = _Run(req, self.device, self.precision, self.sr_args)
                     run.result.admitted_at = now
                     used += footprint_bytes(req)
-                    th = threading.Thread(target=run.loop, args=(batcher, t0, on_done), daemon=True)
+                    if partition is not None:
+                        partition.add(req)
+                    th = threading.Thread(target=run.loop, args=(batcher, t0, on_done, partition), daemon=True)
                     running[req.rid] = th
                     self.events.append((now, 'admit', req.rid))
                     th.start()

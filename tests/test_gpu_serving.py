@@ -63,3 +63,29 @@ def test_admission_waits_for_memory():
     retire0 = [t for t, k, rid in ev if k == 'retire' and rid == 0][0]
     assert admit1 >= retire0
     assert summary['requests'] == 2
+
+
+@pytest.mark.parametrize('model', ['j1j2', 'tj'])
+def test_sm_limit_changes_no_result(model):
+    """A context held to a few SMs (nqs_set_sm_limit: smaller grids, several
+    chain groups per sampler block) produces bitwise the chains, log psi,
+    E_loc, O_k and SR update of the unlimited context."""
+    import torch
+    from tests.gpu_common import WL, make_ctx
+    w = WL['j1j2_10x10'] if model == 'j1j2' else WL['tj_12x12']
+    over = {'n_layers': 3} if model == 'j1j2' else {'L': 8, 'n_up': 28, 'n_down': 28, 'n_layers': 3, 'channels': 16}
+    outs = []
+    for limit in (0, 6):
+        ctx, _ = make_ctx(w, seed=5, **over)
+        ctx.set_sm_limit(limit)
+        cfg, lp = ctx.sample(200, 2, 1, 3, 'bf16')
+        e = ctx.local_energy(cfg, None, 'bf16')
+        O = ctx.logpsi_grad(cfg, 'bf16')
+        delta, info = ctx.sr_solve(O, e, eps=1e-3, rtol=1e-8, max_iter=500, lr=0.01, apply_update=False)
+        ctx.sync()
+        outs.append((cfg, lp, e, O, delta))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+    nqs = lib()
+    with pytest.raises(nqs.NQSError):
+        ctx.set_sm_limit(100000)
