@@ -53,6 +53,7 @@ constexpr int kTcThreads = 32 * (kMaxEpiWarps + kIssuers);
 // sampler is compiled for two blocks at both widths.
 template <int C> constexpr int kMinBlocks = C == 16 ? 2 : 1;
 constexpr int kMaxTiles = 16;
+constexpr int kPropWindow = 16;   // sampler: proposal steps drawn at once
 constexpr int kMaxSlots = 2;
 constexpr uint32_t kNone = 0xFFFFu;
 
@@ -856,12 +857,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     const int G = pl.G, N = pl.N, S = pl.slots;
     unsigned char *ex = smem + pl.o_extra;
     int8_t *cur = reinterpret_cast<int8_t *>(ex);                                // [per_block][N]
-    int *pi = reinterpret_cast<int *>(ex + al16(per_block * N));
-    int *pj = pi + per_block;
-    int *list = pj + per_block;                                                  // [S][G + 1]
-    double *pu = reinterpret_cast<double *>(ex + al16(per_block * N) + al16(4 * (2 * per_block + S * (G + 1))));
-    double *ca = pu + per_block;
+    // [2][S][G + 1]: by step parity (step q + 1 is built while slower threads may still read step q's)
+    int *list2 = reinterpret_cast<int *>(ex + al16(per_block * N));
+    double *ca = reinterpret_cast<double *>(ex + al16(per_block * N) + al16(4 * 2 * (S * (G + 1))));
     double *cphi = ca + per_block;
+    // proposals of the next kPropWindow steps of every chain of the group,
+    // drawn in parallel (they do not depend on the chain state): site i,
+    // neighbour j and log u, [step][chain]
+    double *wlu = cphi + per_block;
+    int *wpi = reinterpret_cast<int *>(wlu + kPropWindow * per_block);
+    int *wpj = wpi + kPropWindow * per_block;
     // chain groups: group k = blockIdx.x + j * gridDim.x (one pass when the
     // grid covers every group; fewer blocks when the launch is held to an SM share)
     bool ok = true;
@@ -884,23 +889,33 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
         __syncthreads();
     }
     const int n_sweeps = burn_in + spc * sweeps_between;
+    const int64_t n_steps = (int64_t)n_sweeps * N;
     for (int sweep = 0; ok && sweep < n_sweeps; ++sweep) {
         for (int q = 0; q < N; ++q) {
-            const uint64_t step = step0 + (uint64_t)sweep * N + q;
-            for (int c = threadIdx.x; c < gc; c += blockDim.x) {
-                const Philox4 b = philox((uint64_t)(c0 + c), step, 0, 0, seed, 0);
-                const int i = (int)mulhi64(b.v[0], (uint64_t)N);
-                pi[c] = i;
-                pj[c] = neighbour_dir_tc(i, (int)(b.v[1] >> 62), pl.L);
-                pu[c] = (double)(b.v[2] >> 11) * 0x1.0p-53;
+            const int64_t gstep = (int64_t)sweep * N + q;
+            const int w = (int)(gstep % kPropWindow);
+            if (w == 0) {   // draw the window (one Philox4x64-10 block per chain and step)
+                for (int t = threadIdx.x; t < kPropWindow * gc; t += blockDim.x) {
+                    const int ww = t / gc, c = t - ww * gc;
+                    if (gstep + ww >= n_steps) continue;
+                    const Philox4 b = philox((uint64_t)(c0 + c), step0 + (uint64_t)(gstep + ww), 0, 0, seed, 0);
+                    const int i = (int)mulhi64(b.v[0], (uint64_t)N);
+                    wpi[ww * per_block + c] = i;
+                    wpj[ww * per_block + c] = neighbour_dir_tc(i, (int)(b.v[1] >> 62), pl.L);
+                    const double u = (double)(b.v[2] >> 11) * 0x1.0p-53;
+                    wlu[ww * per_block + c] = u > 0.0 ? log(u) : -INFINITY;
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            int *pi_s = wpi + w * per_block;
+            int *pj_s = wpj + w * per_block;
+            int *list = list2 + (int)(gstep & 1) * S * (G + 1);
             if (threadIdx.x < S) {   // per-slot list of chains whose proposal changes the state
                 const int s = threadIdx.x;
                 int cnt = 0;
                 for (int g = 0; g < G; ++g) {
                     const int c = s * G + g;
-                    if (c < gc && cur[c * N + pi[c]] != cur[c * N + pj[c]]) list[s * (G + 1) + cnt++] = c;
+                    if (c < gc && cur[c * N + pi_s[c]] != cur[c * N + pj_s[c]]) list[s * (G + 1) + cnt++] = c;
                 }
                 list[s * (G + 1) + G] = cnt;
             }
@@ -913,7 +928,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
                 const int s = slot_row / G, m = slot_row - s * G;
                 const int cnt = list[s * (G + 1) + G];
                 const int c = cnt > 0 ? list[s * (G + 1) + (m < cnt ? m : 0)] : 0;
-                const int i = cnt > 0 ? pi[c] : -1, j = cnt > 0 ? pj[c] : -1;
+                const int i = cnt > 0 ? pi_s[c] : -1, j = cnt > 0 ? pj_s[c] : -1;
                 const int src = site == i ? j : (site == j ? i : site);
                 sh.spins[r] = cur[c * N + src];
             }
@@ -925,8 +940,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
                 const int c = list[s * (G + 1) + m];
                 const double an = sh.res[s * 2 * G + m];
                 const double delta = 2.0 * (an - ca[c]);
-                if (delta >= 0.0 || pu[c] < exp(delta)) {
-                    const int i = pi[c], j = pj[c];
+                // u < exp(2 (a' - a)) evaluated as log u < 2 (a' - a), log u drawn with the proposal
+                if (delta >= 0.0 || wlu[w * per_block + c] < delta) {
+                    const int i = pi_s[c], j = pj_s[c];
                     const int8_t t = cur[c * N + i];
                     cur[c * N + i] = cur[c * N + j];
                     cur[c * N + j] = t;
@@ -1062,7 +1078,7 @@ int eloc_extra(const Problem &p) {
 
 int sample_extra(const Problem &p, int G, int slots) {
     const int per = G * slots;
-    return (int)(al16(per * p.N) + al16(4 * (2 * per + slots * (G + 1))) + 24 * per);
+    return (int)(al16(per * p.N) + al16(4 * 2 * (slots * (G + 1))) + 16 * per + 16 * kPropWindow * per);
 }
 
 // Relative throughput of a one-slot plan: useful rows per computed row,
