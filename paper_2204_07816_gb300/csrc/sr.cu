@@ -17,6 +17,9 @@ namespace {
 
 // scalar slots in the workspace
 enum : int { S_ERE = 0, S_EIM, S_RS, S_FNORM, S_DONE, S_ITER, S_MEANRE, S_MEANIM, S_COUNT = 16 };
+// P-vector kernels of a CG iteration run on ceil(P / kPvThreads) blocks (a grid that depends on P only, so the
+// partial sums and their fixed-order reduction do not depend on the device)
+constexpr int kPvThreads = 256;
 
 constexpr int kRowWarps = 8;    // rows per block in the row GEMV
 constexpr int kColThreads = 256;
@@ -120,60 +123,120 @@ __global__ void __launch_bounds__(kColThreads) gemv_cols_kernel(const double *__
     zpart[(int64_t)blockIdx.y * P + k] = (a0 + a1) + (a2 + a3);
 }
 
-// F = sum_chunks zpart / n; x = 0; r = p = F; rs = |r|^2.
-__global__ void __launch_bounds__(kVecThreads) cg_init_kernel(const double *zpart, int nchunks, int P, int64_t n,
-                                                              double *x, double *r, double *p, double rtol, double *sc) {
+// Fixed-order sum of one double per thread over a kPvThreads block (result in every thread).
+__device__ double pv_block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double w = 0.0;
+    if (warp == 0) {
+        w = warp_sum(lane < kPvThreads / 32 ? sh[lane] : 0.0);
+        if (lane == 0) sh[32] = w;
+    }
+    __syncthreads();
+    w = sh[32];
+    __syncthreads();
+    return w;
+}
+
+// Sum of the nb block partials part[0 .. nb), in a fixed order (every thread).
+__device__ double pv_partials(const double *part, int nb, double *sh) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
+    return pv_block_sum(v, sh);
+}
+
+// CG step, part 1: Ap = sum_chunks zpart / n + eps p; block partials of p . Ap.
+__global__ void __launch_bounds__(kPvThreads) cg_ap_kernel(const double *zpart, int nchunks, int P, int64_t n,
+                                                            double eps, const double *p, double *Ap, double *part,
+                                                            const double *sc) {
+    if (sc[S_DONE] != 0.0) return;
     __shared__ double sh[33];
+    const int k = blockIdx.x * kPvThreads + threadIdx.x;
+    double pap = 0.0;
+    if (k < P) {
+        double z = 0.0;
+        for (int c = 0; c < nchunks; ++c) z += zpart[(int64_t)c * P + k];
+        const double a = z / (double)n + eps * p[k];
+        Ap[k] = a;
+        pap = p[k] * a;
+    }
+    pap = pv_block_sum(pap, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = pap;
+}
+
+// Part 2: alpha = rs / (p . Ap); x += alpha p; r -= alpha Ap; block partials of r . r.
+__global__ void __launch_bounds__(kPvThreads) cg_xr_kernel(int P, const double *p, const double *Ap, double *x,
+                                                            double *r, const double *part, double *part2,
+                                                            const double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    __shared__ double sh[33];
+    const double alpha = sc[S_RS] / pv_partials(part, gridDim.x, sh);
+    const int k = blockIdx.x * kPvThreads + threadIdx.x;
+    double rn = 0.0;
+    if (k < P) {
+        x[k] = fma(alpha, p[k], x[k]);
+        const double rk = fma(-alpha, Ap[k], r[k]);
+        r[k] = rk;
+        rn = rk * rk;
+    }
+    rn = pv_block_sum(rn, sh);
+    if (threadIdx.x == 0) part2[blockIdx.x] = rn;
+}
+
+// Part 3: beta = (r . r) / rs; p = r + beta p.
+__global__ void __launch_bounds__(kPvThreads) cg_dir_kernel(int P, const double *r, double *p, const double *part2,
+                                                             const double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    __shared__ double sh[33];
+    const double beta = pv_partials(part2, gridDim.x, sh) / sc[S_RS];
+    const int k = blockIdx.x * kPvThreads + threadIdx.x;
+    if (k < P) p[k] = fma(beta, p[k], r[k]);
+}
+
+// Part 4 (one block): iteration count, rs = r . r, convergence.
+__global__ void __launch_bounds__(kPvThreads) cg_scalars_kernel(int nb, double rtol, int max_iter,
+                                                                 const double *part2, double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    __shared__ double sh[33];
+    const double rn = pv_partials(part2, nb, sh);
+    if (threadIdx.x == 0) {
+        const double it = sc[S_ITER] + 1.0;
+        sc[S_ITER] = it;
+        sc[S_RS] = rn;
+        if (sqrt(rn) <= rtol * sc[S_FNORM] || it >= (double)max_iter || !isfinite(rn)) sc[S_DONE] = 1.0;
+    }
+}
+
+// CG start: F = sum_chunks zpart / n; x = 0; r = p = F; block partials of |F|^2.
+__global__ void __launch_bounds__(kPvThreads) cg_init_kernel(const double *zpart, int nchunks, int P, int64_t n,
+                                                              double *x, double *r, double *p, double *part) {
+    __shared__ double sh[33];
+    const int k = blockIdx.x * kPvThreads + threadIdx.x;
     double acc = 0.0;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    if (k < P) {
         double f = 0.0;
         for (int c = 0; c < nchunks; ++c) f += zpart[(int64_t)c * P + k];
         f /= (double)n;
         x[k] = 0.0;
         r[k] = f;
         p[k] = f;
-        acc = fma(f, f, acc);
+        acc = f * f;
     }
-    const double rs = vec_block_sum(acc, sh);
+    acc = pv_block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// CG start (one block): rs = |F|^2, |F|, nothing to do if F = 0.
+__global__ void __launch_bounds__(kPvThreads) cg_init_scalars_kernel(int nb, const double *part, double *sc) {
+    __shared__ double sh[33];
+    const double rs = pv_partials(part, nb, sh);
     if (threadIdx.x == 0) {
         sc[S_RS] = rs;
         sc[S_FNORM] = sqrt(rs);
         sc[S_DONE] = (rs == 0.0) ? 1.0 : 0.0;
-    }
-}
-
-// One CG update given z = Ohat^T y_c in zpart.
-__global__ void __launch_bounds__(kVecThreads) cg_step_kernel(const double *zpart, int nchunks, int P, int64_t n,
-                                                              double eps, double rtol, int max_iter, double *x,
-                                                              double *r, double *p, double *Ap, double *sc) {
-    if (sc[S_DONE] != 0.0) return;
-    __shared__ double sh[33];
-    double pap = 0.0;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        double z = 0.0;
-        for (int c = 0; c < nchunks; ++c) z += zpart[(int64_t)c * P + k];
-        const double a = z / (double)n + eps * p[k];
-        Ap[k] = a;
-        pap = fma(p[k], a, pap);
-    }
-    pap = vec_block_sum(pap, sh);
-    const double rs = sc[S_RS];
-    const double alpha = rs / pap;
-    double rn = 0.0;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        x[k] = fma(alpha, p[k], x[k]);
-        const double rk = fma(-alpha, Ap[k], r[k]);
-        r[k] = rk;
-        rn = fma(rk, rk, rn);
-    }
-    rn = vec_block_sum(rn, sh);
-    const double beta = rn / rs;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) p[k] = fma(beta, p[k], r[k]);
-    if (threadIdx.x == 0) {
-        const double it = sc[S_ITER] + 1.0;
-        sc[S_ITER] = it;
-        sc[S_RS] = rn;
-        if (sqrt(rn) <= rtol * sc[S_FNORM] || it >= (double)max_iter || !isfinite(rn)) sc[S_DONE] = 1.0;
     }
 }
 
@@ -191,8 +254,8 @@ int chunks_for(int64_t rows, int P, int num_sms) {
 }  // namespace
 
 size_t sr_workspace_doubles(int64_t n, int P) {
-    // y [2n], Ap, r, p [P], zpart [256][P] upper bound, scalars
-    return 2 * (size_t)n + 3 * (size_t)P + 256 * (size_t)P + S_COUNT;
+    // y [2n], Ap, r, p [P], zpart [256][P] upper bound, scalars, two block-partial arrays
+    return 2 * (size_t)n + 3 * (size_t)P + 256 * (size_t)P + S_COUNT + 2 * (size_t)((P + kPvThreads - 1) / kPvThreads);
 }
 
 int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t n, double eps, double rtol,
@@ -208,15 +271,19 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     double *p = r + P;
     double *zpart = p + P;
     double *sc = zpart + (size_t)256 * P;
+    const int pvb = (P + kPvThreads - 1) / kPvThreads;
+    double *part = sc + S_COUNT;
+    double *part2 = part + pvb;
     cudaStream_t s = env.stream;
     const dim3 cgrid((P + kColThreads - 1) / kColThreads, nchunks);
     const int rgrid = (int)((rows + kRowWarps - 1) / kRowWarps);
 
     energy_kernel<<<1, kVecThreads, 0, s>>>(eloc, n, y, sc);
     gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
-    cg_init_kernel<<<1, kVecThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, rtol, sc);
+    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, part);
+    cg_init_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
     if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR setup launch failed"; return NQS_ERR_CUDA; }
-    *env.launches += 3;
+    *env.launches += 4;
 
     double host_sc[S_COUNT];
     int done_iters = 0;
@@ -226,10 +293,13 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
             gemv_rows_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(O, p, rows, P, y, sc);
             center_kernel<<<1, kVecThreads, 0, s>>>(y, n, sc);
             gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
-            cg_step_kernel<<<1, kVecThreads, 0, s>>>(zpart, nchunks, P, n, eps, rtol, max_iter, delta, r, p, Ap, sc);
+            cg_ap_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, eps, p, Ap, part, sc);
+            cg_xr_kernel<<<pvb, kPvThreads, 0, s>>>(P, p, Ap, delta, r, part, part2, sc);
+            cg_dir_kernel<<<pvb, kPvThreads, 0, s>>>(P, r, p, part2, sc);
+            cg_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, rtol, max_iter, part2, sc);
         }
         done_iters += batch;
-        *env.launches += 4 * batch;
+        *env.launches += 7 * batch;
         cudaError_t e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { *env.msg = std::string("SR loop: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
