@@ -21,6 +21,10 @@ namespace nqs {
 namespace {
 
 constexpr int kGradThreads = 256;
+// Blocks per SM the kernel is compiled for: four at 16 channels (64 registers,
+// no spills; twice the resident warps of the unbounded 108-register build),
+// two at 32 channels (more would spill).
+template <int C> constexpr int kGradMinBlocks = C == 16 ? 4 : 2;
 
 struct GradLayout {
     int NP;                // padded site stride
@@ -45,7 +49,7 @@ __host__ __device__ inline GradLayout grad_layout(const Problem &p) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(kGradThreads) grad_fast_kernel(Problem p, const float *__restrict__ prm,
+__global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_kernel(Problem p, const float *__restrict__ prm,
                                                                 const double *__restrict__ p64,
                                                                 const int8_t *__restrict__ configs, int64_t n,
                                                                 double *__restrict__ O, float *__restrict__ scratch,
