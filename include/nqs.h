@@ -124,6 +124,15 @@ const char *nqs_last_error(const nqs_ctx *ctx);
 /* Wait for the context's stream; return and clear the latched device error. */
 int nqs_sync(nqs_ctx *ctx);
 
+/* Sampler statistics of this context since its creation or the last reset
+ * (waits for the context's stream): moves = proposals whose two sites hold
+ * different values (the others leave the configuration unchanged and count
+ * as rejected steps, Sec. 3.2 reading of the exchange proposal), accepted =
+ * moves accepted by the Metropolis test. The acceptance rate per proposal is
+ * accepted / (chains x sweeps x N). Host int64 outputs (either may be NULL);
+ * reset != 0 zeroes the counters after reading. */
+int nqs_sampler_counts(nqs_ctx *ctx, int64_t *moves, int64_t *accepted, int32_t reset);
+
 /* Size every later launch of this context for `sms` SMs instead of the
  * whole device (0 = whole device, the default; 1 .. SM count), so that
  * contexts running side by side on their own streams (a serving mix) keep

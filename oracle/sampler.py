@@ -62,8 +62,11 @@ def neighbour(i, d, L):
     return ((y + dy) % L) * L + (x + dx) % L
 
 
-def metropolis(params, spec, chains, step0, seed, samples_per_chain, sweeps_between, burn_in):
+def metropolis(params, spec, chains, step0, seed, samples_per_chain, sweeps_between, burn_in, counts=None):
     """Run every chain; returns (samples, logpsi, chains, a, phi, step).
+
+    counts (optional dict) accumulates 'moves' (proposals whose two sites
+    differ) and 'accepted' (moves the Metropolis test accepts).
 
     chains [n_chains, N] int8 is the start state (not modified). step0 is the
     number of proposals the chains have already made. samples is
@@ -102,6 +105,9 @@ def metropolis(params, spec, chains, step0, seed, samples_per_chain, sweeps_betw
             delta = 2.0 * (a_new - a[idx])
             with np.errstate(over='ignore'):
                 acc = (delta >= 0.0) | (u[idx] < np.exp(np.minimum(delta, 0.0)))
+            if counts is not None:
+                counts['moves'] = counts.get('moves', 0) + int(idx.size)
+                counts['accepted'] = counts.get('accepted', 0) + int(acc.sum())
             sel = idx[acc]
             chains[sel] = prop[acc]
             a[sel] = a_new[acc]

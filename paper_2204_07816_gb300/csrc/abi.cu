@@ -20,7 +20,7 @@ struct nqs_ctx {
     int num_sms = 0;
     int sm_limit = 0;              // 0: whole device; else grids are sized for this many SMs
     size_t max_smem = 0;
-    int *err_dev = nullptr;        // device error bits
+    int *err_dev = nullptr;        // device error bits (int), then at +16 B the sampler counters (2 x u64)
     float *params32 = nullptr;     // float copy for the FP32 path
     void *packed = nullptr;        // tensor-core operand images
     int8_t *chains = nullptr;
@@ -91,6 +91,7 @@ LaunchEnv env_of(nqs_ctx *c) {
     e.num_sms = sms_of(c);
     e.max_smem = c->max_smem;
     e.err = c->err_dev;
+    e.moves = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->err_dev) + 16);
     e.launches = &c->launches;
     e.msg = &c->msg;
     return e;
@@ -179,8 +180,8 @@ int nqs_init(nqs_ctx **out, const nqs_problem *q, double *params, uint64_t seed,
     }
     c->num_sms = prop.multiProcessorCount;
     c->max_smem = prop.sharedMemPerBlockOptin;
-    e = cudaMalloc(&c->err_dev, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    e = cudaMalloc(&c->err_dev, 32);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, 32, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&c->params32, sizeof(float) * c->p.P);
     if (e == cudaSuccess) {
         const size_t pk = tc_packed_bytes(c->p);
@@ -207,6 +208,22 @@ int nqs_sync(nqs_ctx *c) {
         if (bits & ERRBIT_NONFINITE) return fail(c, NQS_ERR_NONFINITE, "a kernel produced a non-finite value");
         if (bits & ERRBIT_TIMEOUT) return fail(c, NQS_ERR_TIMEOUT, "a device-side wait ran out of iterations");
         return fail(c, NQS_ERR_CUDA, "a device-side bounds check failed");
+    }
+    return NQS_OK;
+}
+
+int nqs_sampler_counts(nqs_ctx *c, int64_t *moves, int64_t *accepted, int32_t reset) {
+    if (int rc = check_ctx(c)) return rc;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    unsigned long long h[2] = {0, 0};
+    e = cudaMemcpy(h, reinterpret_cast<char *>(c->err_dev) + 16, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sampler counters");
+    if (moves) *moves = (int64_t)h[0];
+    if (accepted) *accepted = (int64_t)h[1];
+    if (reset) {
+        e = cudaMemset(reinterpret_cast<char *>(c->err_dev) + 16, 0, sizeof(h));
+        if (e != cudaSuccess) return cuda_fail(c, e, "sampler counters");
     }
     return NQS_OK;
 }

@@ -16,6 +16,7 @@ struct LaunchEnv {
     int num_sms;
     size_t max_smem;     // opt-in shared memory per block
     int *err;            // device error bits
+    unsigned long long *moves = nullptr;   // sampler counters [2]: moves that change the state, accepted moves
     int64_t *launches;   // kernels launched so far by this context
     std::string *msg;    // host error text
 };

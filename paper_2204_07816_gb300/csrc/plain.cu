@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
                                                                 int8_t *chains, int n_chains, uint64_t step0,
                                                                 uint64_t seed, int spc, int sweeps_between,
                                                                 int burn_in, int8_t *out_cfg, double *out_logpsi,
-                                                                PlainLayout lay, int *err) {
+                                                                PlainLayout lay, int *err,
+                                                                unsigned long long *moves) {
     extern __shared__ __align__(16) unsigned char smem[];
     PlainNet<T> net;
     net.bind(smem, lay);
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
     __syncthreads();
 
     const int n_sweeps = burn_in + spc * sweeps_between;
+    unsigned long long n_moves = 0, n_acc = 0;
     for (int sweep = 0; sweep < n_sweeps; ++sweep) {
         for (int q = 0; q < N; ++q) {
             const uint64_t step = step0 + (uint64_t)sweep * N + q;
@@ -277,7 +279,9 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
                 for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
                     const int g = list[m];
                     const double delta = 2.0 * (net.a[m] - ca[g]);
+                    ++n_moves;
                     if (delta >= 0.0 || pu[g] < exp(delta)) {
+                        ++n_acc;
                         const int i = pi[g], j = pj[g];
                         const int8_t t = cur[g * N + i];
                         cur[g * N + i] = cur[g * N + j];
@@ -304,6 +308,10 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
         }
     }
     for (int r = threadIdx.x; r < gc * N; r += blockDim.x) chains[(size_t)c0 * N + r] = cur[r];
+    if (moves && n_moves) {
+        atomicAdd(&moves[0], n_moves);
+        atomicAdd(&moves[1], n_acc);
+    }
 }
 
 // ------------------------------------------------------------------ backward
@@ -553,7 +561,7 @@ static int sample_plain_t(const Problem &p, const T *params, const double *p64, 
         int rc = set_smem<T>(k, bytes, env);
         if (rc) return rc;
         k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, chains, n_chains, step0, seed, spc, sb, burn,
-                                                 out_cfg, out_logpsi, lay, env.err);
+                                                 out_cfg, out_logpsi, lay, env.err, env.moves);
     });
     return check_launch(env, "sample_plain_kernel");
 }

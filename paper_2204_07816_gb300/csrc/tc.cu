@@ -849,7 +849,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
                                                                    int8_t *chains, int n_chains, int per_block,
                                                                    uint64_t step0, uint64_t seed, int spc,
                                                                    int sweeps_between, int burn_in, int8_t *out_cfg,
-                                                                   double *out_logpsi, int *err) {
+                                                                   double *out_logpsi, int *err,
+                                                                   unsigned long long *moves) {
     extern __shared__ __align__(128) unsigned char smem[];
     TcShared sh;
     TcState st;
@@ -870,6 +871,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     // chain groups: group k = blockIdx.x + j * gridDim.x (one pass when the
     // grid covers every group; fewer blocks when the launch is held to an SM share)
     bool ok = true;
+    unsigned long long n_moves = 0, n_acc = 0;
     for (int c0 = blockIdx.x * per_block; ok && c0 < n_chains; c0 += gridDim.x * per_block) {
     const int gc = min(per_block, n_chains - c0);
     {
@@ -940,8 +942,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
                 const int c = list[s * (G + 1) + m];
                 const double an = sh.res[s * 2 * G + m];
                 const double delta = 2.0 * (an - ca[c]);
+                ++n_moves;
                 // u < exp(2 (a' - a)) evaluated as log u < 2 (a' - a), log u drawn with the proposal
                 if (delta >= 0.0 || wlu[w * per_block + c] < delta) {
+                    ++n_acc;
                     const int i = pi_s[c], j = pj_s[c];
                     const int8_t t = cur[c * N + i];
                     cur[c * N + i] = cur[c * N + j];
@@ -969,6 +973,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     if (ok)
         for (int r = threadIdx.x; r < gc * N; r += blockDim.x) chains[(size_t)c0 * N + r] = cur[r];
     __syncthreads();
+    }
+    if (moves && n_moves) {
+        atomicAdd(&moves[0], n_moves);
+        atomicAdd(&moves[1], n_acc);
     }
     tc_teardown(pl, sh, st);
 }
@@ -1338,7 +1346,7 @@ int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_
         k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, (const unsigned char *)packed, chains,
                                                                     n_chains, per_block, step0, seed, spc,
                                                                     sweeps_between, burn_in, out_cfg, out_logpsi,
-                                                                    env.err);
+                                                                    env.err, env.moves);
     });
     return check(env, "sample_tc_kernel");
 }

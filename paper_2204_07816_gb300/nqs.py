@@ -26,7 +26,7 @@ MODEL = {'j1j2': 0, 'tj': 1}
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
-           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_set_sm_limit')
+           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_set_sm_limit', 'nqs_sampler_counts')
 
 
 class nqs_problem(ctypes.Structure):
@@ -64,6 +64,7 @@ def load(path=LIB_PATH):
         'nqs_kernel_launches': (I64, [P]),
         'nqs_probe_wait_timeout': (ctypes.c_int, [P, I64]),
         'nqs_set_sm_limit': (ctypes.c_int, [P, I32]),
+        'nqs_sampler_counts': (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), I32]),
         'nqs_logpsi': (ctypes.c_int, [P, P, I64, P, I32]),
         'nqs_connected': (ctypes.c_int, [P, P, I64, I32, P, P, P, P]),
         'nqs_local_energy': (ctypes.c_int, [P, P, P, I64, P, I32]),
@@ -266,6 +267,12 @@ class Context:
                                         _ptr(cfg, torch.int8, 'configs_out'), _ptr(lp, torch.float64, 'logpsi_out'),
                                         _prec(precision)))
         return cfg, lp
+
+    def sampler_counts(self, reset=False):
+        """nqs_sampler_counts: (moves, accepted) since creation or the last reset."""
+        mv, ac = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.nqs_sampler_counts(self.ctx, ctypes.byref(mv), ctypes.byref(ac), int(bool(reset))))
+        return mv.value, ac.value
 
     def set_sm_limit(self, sms):
         """nqs_set_sm_limit: size later launches for `sms` SMs (0 = all)."""

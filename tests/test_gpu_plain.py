@@ -172,8 +172,12 @@ def test_sampler_chains_bit_exact_fp64(prec):
     spec, _ = oracle_of(w)
     cfg, lp = ctx.sample(16, 8, 1, 4, prec)
     ch0 = sampler.init_chains(3, 16, sampler.canonical_values(16, 8, 8))
-    want_cfg, want_lp, ch_end, _, _, step = sampler.metropolis(params, spec, ch0, 0, 3, 8, 1, 4)
+    counts = {}
+    want_cfg, want_lp, ch_end, _, _, step = sampler.metropolis(params, spec, ch0, 0, 3, 8, 1, 4, counts=counts)
     assert np.array_equal(cfg.cpu().numpy(), want_cfg)
+    # move and acceptance counters: exactly the oracle's
+    assert ctx.sampler_counts(reset=True) == (counts['moves'], counts['accepted'])
+    assert ctx.sampler_counts() == (0, 0)
     assert rel_err(lp.cpu().numpy(), want_lp) <= 1e-12
     chains, gstep = ctx.get_chains(16)
     assert gstep == step and np.array_equal(chains.cpu().numpy(), ch_end)

@@ -176,3 +176,25 @@ def test_sampler_bf16_conserves_sector_tj():
     # the stored log psi is the bf16 log psi of the stored configuration
     again = ctx.logpsi(cfg, 'bf16')
     assert torch.equal(again, lp)
+
+
+def test_sampler_counts_bf16():
+    """Move and acceptance counters of the tensor-core sampler: accepted <= moves
+    <= proposals, and with all-zero weights (|psi| uniform) every move is
+    accepted."""
+    w = WL['j1j2_4x4']
+    over = {'channels': 16, 'n_layers': 3}
+    ctx, _ = make_ctx(w, **over)
+    ctx.sample(64, 4, 1, 2, 'bf16')
+    moves, acc = ctx.sampler_counts(reset=True)
+    assert 0 < acc <= moves <= 64 * 6 * 16
+    zero = np.zeros(nqs_param_count_of(w, **over))
+    ctx0, _ = make_ctx(w, params=zero, **over)
+    ctx0.sample(64, 4, 1, 2, 'bf16')
+    m0, a0 = ctx0.sampler_counts()
+    assert m0 > 0 and a0 == m0
+
+
+def nqs_param_count_of(w, **over):
+    from tests.gpu_common import problem_of
+    return lib().nqs_param_count(problem_of(w, **over))

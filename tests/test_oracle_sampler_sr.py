@@ -231,3 +231,36 @@ def test_uniform_weights_equal_plain_means(small_sr):
     F1, e1 = sr.force(dA, dPhi, e)
     F2, e2 = sr.force(dA, dPhi, e, weights=np.full(e.size, 3.0))
     assert np.allclose(F1, F2, rtol=1e-13, atol=1e-16) and abs(e1 - e2) < 1e-13
+
+
+def test_oracle_sampler_counts():
+    """Move/acceptance counting in the oracle sampler: moves <= proposals,
+    accepted <= moves; all-zero weights accept every move; the counts do not
+    change the chains."""
+    from oracle import cnn, sampler
+    spec = cnn.NetSpec(L=4, c_in=1, channels=4, n_layers=2)
+    rng = np.random.default_rng(5)
+    params = 0.8 * rng.normal(size=cnn.param_count(spec))
+    ch0 = sampler.init_chains(3, 32, sampler.canonical_values(16, 8, 8))
+    counts = {}
+    a = sampler.metropolis(params, spec, ch0, 0, 3, 2, 1, 2, counts=counts)
+    b = sampler.metropolis(params, spec, ch0, 0, 3, 2, 1, 2)
+    assert np.array_equal(a[0], b[0])
+    assert 0 < counts['accepted'] <= counts['moves'] <= 32 * 4 * 16
+    c0 = {}
+    sampler.metropolis(np.zeros_like(params), spec, ch0, 0, 3, 2, 1, 2, counts=c0)
+    assert c0['accepted'] == c0['moves'] > 0
+    # a flat |psi| accepts every move, so the chains follow the proposals alone:
+    # recount the moves one proposal at a time with Python integers
+    moves = 0
+    for c in range(32):
+        s = [int(v) for v in ch0[c]]
+        for step in range(4 * 16):
+            b0, b1, _, _ = philox.philox_block((c, step, 0, 0), (3, 0))
+            i = (b0 * 16) >> 64
+            dx, dy = ((1, 0), (-1, 0), (0, 1), (0, -1))[b1 >> 62]
+            j = ((i // 4 + dy) % 4) * 4 + (i % 4 + dx) % 4
+            if s[i] != s[j]:
+                moves += 1
+                s[i], s[j] = s[j], s[i]
+    assert c0['moves'] == moves
