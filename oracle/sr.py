@@ -20,7 +20,11 @@ F = Ohat^T Ehat / N_s.
 
 The paper forms S explicitly and factorises it; this oracle offers that
 (dense solve) and conjugate gradient on the same system with the stopping
-rule ||r||_2 <= rtol * ||F||_2 from x0 = 0.
+rule ||r||_2 <= rtol * ||F||_2 from x0 = 0, and the sample-space form
+(solve_woodbury): since (Ohat^T Ohat / N_s + eps I)^-1 Ohat^T
+= Ohat^T (Ohat Ohat^T / N_s + eps I)^-1, the same delta is
+Ohat^T y with (Ohat Ohat^T / N_s + eps I) y = Ehat / N_s, a 2 N_s x 2 N_s
+system in place of the P x P one.
 """
 
 import numpy as np
@@ -68,6 +72,19 @@ def solve_dense(dA, dPhi, eloc, eps):
     F, e_mean = force(dA, dPhi, eloc)
     S = s_matrix(dA, dPhi)
     return np.linalg.solve(S + eps * np.eye(S.shape[0]), F), e_mean
+
+
+def solve_woodbury(dA, dPhi, eloc, eps):
+    """delta from the 2 N_s x 2 N_s sample-space system (eps > 0); returns
+    (delta, <E>)."""
+    eloc = np.asarray(eloc, dtype=np.complex128)
+    e_mean = eloc.mean()
+    Oh = centred_stack(dA, dPhi)
+    ns = eloc.size
+    eh = np.concatenate([(eloc - e_mean).real, (eloc - e_mean).imag])
+    T = Oh @ Oh.T / ns
+    y = np.linalg.solve(T + eps * np.eye(2 * ns), eh / ns)
+    return Oh.T @ y, e_mean
 
 
 def s_times(Oh, ns, eps, x):

@@ -160,6 +160,19 @@ def test_cg_matches_dense_solve(small_sr):
     assert em == em2
 
 
+@pytest.mark.parametrize('n_s', [16, 64, 1024])
+def test_woodbury_equals_dense_solve(small_sr, n_s):
+    """The sample-space system gives the delta of the parameter-space one:
+    fewer samples than parameters (2 N_s < P = 196), about equal, and more."""
+    dA, dPhi, e = small_sr
+    dA, dPhi, e = dA[:n_s], dPhi[:n_s], e[:n_s]
+    for eps in (1e-4, 1e-2):
+        d_dense, em = sr.solve_dense(dA, dPhi, e, eps)
+        d_wb, em2 = sr.solve_woodbury(dA, dPhi, e, eps)
+        assert np.linalg.norm(d_wb - d_dense) <= 1e-9 * np.linalg.norm(d_dense)
+        assert abs(em - em2) <= 1e-14 * abs(em)
+
+
 def test_large_shift_limit(small_sr):
     dA, dPhi, e = small_sr
     F, _ = sr.force(dA, dPhi, e)
