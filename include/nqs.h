@@ -271,6 +271,23 @@ int nqs_sr_solve(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, d
                  int32_t max_iter, double lr, double *delta_out, int32_t *iters_out, double *resid_out,
                  double *energy_out, int32_t apply_update);
 
+/* The same delta from the sample-space system (the paper forms a
+ * covariance matrix and factorises it, Sec. 5.4.1; here the 2n x 2n one):
+ *   Ohat = [Re Oc; Im Oc] ([2n][P]), Ehat = [Re(E - <E>); Im(E - <E>)],
+ *   (Ohat Ohat^T / n + eps I) y = Ehat / n   (Cholesky, FP64),
+ *   delta = Ohat^T y,
+ * equal to the solution of (S + eps I) delta = F because
+ * (Ohat^T Ohat / n + eps I)^-1 Ohat^T = Ohat^T (Ohat Ohat^T / n + eps I)^-1.
+ * Work: (2n)^2 P + (2n)^3 / 3 multiply-adds, against 4 n P per CG
+ * iteration, so it pays when CG needs more than about n / 2 iterations.
+ * Arguments as nqs_sr_solve; eps must be > 0 and n <= 32,768 (workspace
+ * (2n)^2 float64, owned by the context). resid_out (HOST) receives
+ * ||(S + eps I) delta - F|| / ||F||, evaluated matrix-free after the solve.
+ * Returns NQS_ERR_NONFINITE if a pivot was not positive or a value is not
+ * finite; the update is then not applied. */
+int nqs_sr_solve_woodbury(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, double eps, double lr,
+                          double *delta_out, double *resid_out, double *energy_out, int32_t apply_update);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/nqs.h): context lifetime,
 // argument validation, workspace and chain-state ownership, dispatch to the
 // CUDA-core and tensor-core kernels.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -37,6 +38,8 @@ struct nqs_ctx {
 namespace {
 
 const char *kNoCtx = "no context";
+// sample-space SR: the 2n x 2n float64 matrix of n = 32,768 samples takes 34 GB
+constexpr int64_t kWoodburyMaxSamples = 32768;
 thread_local std::string g_init_error;
 
 int fail(nqs_ctx *c, int code, const std::string &m) {
@@ -470,6 +473,23 @@ int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, dou
     const int rc = run_sr_solve(c->p, O, eloc, n, eps, rtol, max_iter, lr, delta, c->params, apply_update,
                                 (double *)c->scratch, &iters, &resid, energy, env);
     if (iters_out) *iters_out = iters;
+    if (resid_out) *resid_out = resid;
+    if (energy_out) { energy_out[0] = energy[0]; energy_out[1] = energy[1]; }
+    return rc;
+}
+
+int nqs_sr_solve_woodbury(nqs_ctx *c, const double *O, const double *eloc, int64_t n, double eps, double lr,
+                          double *delta, double *resid_out, double *energy_out, int32_t apply_update) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n <= 0 || !O || !eloc || !delta) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: bad arrays");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: eps must be > 0");
+    if (n > kWoodburyMaxSamples) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: n_s above the limit");
+    if (int rc = ensure_scratch(c, sr_woodbury_workspace_doubles(n, c->p.P) * sizeof(double))) return rc;
+    LaunchEnv env = env_of(c);
+    env.num_sms = c->num_sms;
+    double resid = 0.0, energy[2] = {0.0, 0.0};
+    const int rc = run_sr_woodbury(c->p, O, eloc, n, eps, lr, delta, c->params, apply_update, (double *)c->scratch,
+                                   &resid, energy, env);
     if (resid_out) *resid_out = resid;
     if (energy_out) { energy_out[0] = energy[0]; energy_out[1] = energy[1]; }
     return rc;

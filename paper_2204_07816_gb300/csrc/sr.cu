@@ -5,6 +5,12 @@
 // with Ohat the real-stacked [2n, P] matrix of local derivatives, and the
 // system is solved by conjugate gradient. Every reduction runs in a fixed
 // order, so results do not depend on what else runs on the GPU.
+//
+// Sample-space form (run_sr_woodbury): the same delta is
+//   delta = Ohat^T y,   (Ohat Ohat^T / n + eps I) y = Ehat / n,
+// since (Ohat^T Ohat / n + eps I)^-1 Ohat^T = Ohat^T (Ohat Ohat^T / n + eps I)^-1.
+// The 2n x 2n matrix is formed (centred Gram matrix, lower triangle) and
+// factorised by a blocked right-looking Cholesky, as the paper factorises S.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -16,7 +22,7 @@ namespace nqs {
 namespace {
 
 // scalar slots in the workspace
-enum : int { S_ERE = 0, S_EIM, S_RS, S_FNORM, S_DONE, S_ITER, S_MEANRE, S_MEANIM, S_COUNT = 16 };
+enum : int { S_ERE = 0, S_EIM, S_RS, S_FNORM, S_DONE, S_ITER, S_MEANRE, S_MEANIM, S_WBRES, S_COUNT = 16 };
 // P-vector kernels of a CG iteration run on ceil(P / kPvThreads) blocks (a grid that depends on P only, so the
 // partial sums and their fixed-order reduction do not depend on the device)
 constexpr int kPvThreads = 256;
@@ -240,6 +246,236 @@ __global__ void __launch_bounds__(kPvThreads) cg_init_scalars_kernel(int nb, con
     }
 }
 
+// ---------------------------------------------------------------- sample-space (Woodbury) form
+constexpr int kWb = 64;          // tile edge of the Gram matrix, Cholesky block size
+constexpr int kWbK = 16;         // K chunk staged in shared memory by the tile kernel
+constexpr int kWbThreads = 256;  // 16 x 16 threads, 4 x 4 outputs each
+
+// Lower-triangular tile number t -> (row tile, column tile), column <= row.
+__device__ __forceinline__ void tri_tile(int64_t t, int *bi, int *bj) {
+    int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+    while ((int64_t)i * (i + 1) / 2 > t) --i;
+    *bi = i;
+    *bj = (int)(t - (int64_t)i * (i + 1) / 2);
+}
+
+// kGram: A[i, j] = sum_k Oc[i, k] Oc[j, k] / n + eps [i == j] over k < P, for
+//   the lower tiles, Oc = O minus the column mean of its half (rows < n: real
+//   parts, rows >= n: imaginary parts).
+// !kGram (trailing update of Cholesky step kb): A[i, j] -= sum_k L[i, k] L[j, k]
+//   over the 64 columns of block kb, for the lower tiles right of and below
+//   block kb.
+template <bool kGram>
+__global__ void __launch_bounds__(kWbThreads) wb_tile_kernel(const double *__restrict__ X, int64_t ldx, int64_t K,
+                                                             const double *__restrict__ mu, int64_t n, double eps,
+                                                             double *A, int64_t m, int kb) {
+    __shared__ double sa[kWbK][kWb + 1];
+    __shared__ double sb[kWbK][kWb + 1];
+    int bi, bj;
+    tri_tile(blockIdx.x, &bi, &bj);
+    if (!kGram) { bi += kb + 1; bj += kb + 1; }
+    const int64_t i0 = (int64_t)bi * kWb, j0 = (int64_t)bj * kWb;
+    const int64_t k_begin = kGram ? 0 : (int64_t)kb * kWb;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int64_t k0 = 0; k0 < K; k0 += kWbK) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = threadIdx.x + e * kWbThreads;   // 0 .. 1023
+            const int r = idx >> 4, c = idx & 15;
+            const int64_t k = k0 + c;
+            double va = 0.0, vb = 0.0;
+            if (k < K) {
+                const int64_t ri = i0 + r, rj = j0 + r;
+                if (ri < m) {
+                    va = X[ri * ldx + k_begin + k];
+                    if (kGram) va -= mu[(ri >= n ? K : 0) + k];
+                }
+                if (rj < m) {
+                    vb = X[rj * ldx + k_begin + k];
+                    if (kGram) vb -= mu[(rj >= n ? K : 0) + k];
+                }
+            }
+            sa[c][r] = va;
+            sb[c][r] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kWbK; ++c) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = sa[c][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = sb[c][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t i = i0 + ty + 16 * a;
+        if (i >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t j = j0 + tx + 16 * b;
+            if (j >= m || j > i) continue;
+            if (kGram) A[i * m + j] = acc[a][b] / (double)n + (i == j ? eps : 0.0);
+            else A[i * m + j] -= acc[a][b];
+        }
+    }
+}
+
+// Cholesky of the diagonal block kb (already updated by the earlier steps), in
+// shared memory, column by column. A pivot that is not positive becomes NaN,
+// which reaches delta and is reported as a non-finite result.
+__global__ void __launch_bounds__(kWbThreads) wb_potrf_kernel(double *A, int64_t m, int kb) {
+    __shared__ double s[kWb][kWb + 1];
+    const int64_t o = (int64_t)kb * kWb;
+    const int nb = (int)std::min<int64_t>(kWb, m - o);
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int i = idx / nb, j = idx % nb;
+        s[i][j] = j <= i ? A[(o + i) * m + o + j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = s[j][j];
+            s[j][j] = d > 0.0 ? sqrt(d) : __longlong_as_double(0x7ff8000000000000LL);
+        }
+        __syncthreads();
+        const double piv = s[j][j];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) s[i][j] /= piv;
+        __syncthreads();
+        const int w = nb - j - 1;
+        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+            const int i = j + 1 + idx / w, k = j + 1 + idx % w;
+            if (k <= i) s[i][k] = fma(-s[i][j], s[k][j], s[i][k]);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int i = idx / nb, j = idx % nb;
+        if (j <= i) A[(o + i) * m + o + j] = s[i][j];
+    }
+}
+
+// Panel below the diagonal block kb: L[i, block kb] = A[i, block kb] L_kk^-T,
+// one thread per row (forward substitution along the row).
+__global__ void __launch_bounds__(kWb) wb_trsm_kernel(double *A, int64_t m, int kb) {
+    __shared__ double row[kWb][kWb + 1];
+    const int64_t o = (int64_t)kb * kWb;
+    const int64_t i = o + (int64_t)(blockIdx.x + 1) * kWb + threadIdx.x;
+    const double *Lkk = A + o * m + o;
+    if (i < m) {
+        double *ai = A + i * m + o;
+        for (int j = 0; j < kWb; ++j) {
+            double v = ai[j];
+            for (int l = 0; l < j; ++l) v = fma(-row[threadIdx.x][l], __ldg(Lkk + (int64_t)j * m + l), v);
+            v /= __ldg(Lkk + (int64_t)j * m + j);
+            row[threadIdx.x][j] = v;
+        }
+        for (int j = 0; j < kWb; ++j) ai[j] = row[threadIdx.x][j];
+    }
+}
+
+// Forward substitution L z = b, block kb: solve the diagonal block in place.
+__global__ void __launch_bounds__(kWb) wb_fwd_diag_kernel(const double *A, int64_t m, int kb, double *b) {
+    __shared__ double z[kWb];
+    const int64_t o = (int64_t)kb * kWb;
+    const int nb = (int)std::min<int64_t>(kWb, m - o);
+    const int t = threadIdx.x;
+    if (t < nb) z[t] = b[o + t];
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (t == j) z[j] /= A[(o + j) * m + o + j];
+        __syncthreads();
+        if (t > j && t < nb) z[t] = fma(-A[(o + t) * m + o + j], z[j], z[t]);
+        __syncthreads();
+    }
+    if (t < nb) b[o + t] = z[t];
+}
+
+// ... then b[i] -= L[i, block kb] . z[block kb] for the rows below (one warp per row).
+__global__ void __launch_bounds__(kRowWarps * 32) wb_fwd_update_kernel(const double *A, int64_t m, int kb, double *b) {
+    const int64_t o = (int64_t)kb * kWb;
+    const int64_t i = o + kWb + (int64_t)blockIdx.x * kRowWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= m) return;
+    const double *li = A + i * m + o;
+    double v = fma(li[lane], b[o + lane], li[lane + 32] * b[o + lane + 32]);
+    v = warp_sum(v);
+    if (lane == 0) b[i] -= v;
+}
+
+// Back substitution L^T y = z, block kb: solve the diagonal block in place.
+__global__ void __launch_bounds__(kWb) wb_bwd_diag_kernel(const double *A, int64_t m, int kb, double *b) {
+    __shared__ double y[kWb];
+    const int64_t o = (int64_t)kb * kWb;
+    const int nb = (int)std::min<int64_t>(kWb, m - o);
+    const int t = threadIdx.x;
+    if (t < nb) y[t] = b[o + t];
+    __syncthreads();
+    for (int j = nb - 1; j >= 0; --j) {
+        if (t == j) y[j] /= A[(o + j) * m + o + j];
+        __syncthreads();
+        if (t < j) y[t] = fma(-A[(o + j) * m + o + t], y[j], y[t]);
+        __syncthreads();
+    }
+    if (t < nb) b[o + t] = y[t];
+}
+
+// ... then b[i] -= sum_l L[o + l, i] y[o + l] for the rows above (one thread per row).
+__global__ void __launch_bounds__(256) wb_bwd_update_kernel(const double *A, int64_t m, int kb, double *b) {
+    const int64_t o = (int64_t)kb * kWb;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= o) return;
+    const int nb = (int)std::min<int64_t>(kWb, m - o);
+    double v = 0.0;
+    for (int l = 0; l < nb; ++l) v = fma(A[(o + l) * m + i], b[o + l], v);
+    b[i] -= v;
+}
+
+// b = v / n (the right-hand side Ehat / n), and the all-(1/n) vector used for the column means.
+__global__ void wb_rhs_kernel(const double *v, int64_t m, int64_t n, double *b, double *ones) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        b[i] = v[i] / (double)n;
+        ones[i] = 1.0 / (double)n;
+    }
+}
+
+// out[k] = sum over chunks of zpart[c][k] (fixed order).
+__global__ void wb_chunk_sum_kernel(const double *zpart, int nchunks, int P, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    double z = 0.0;
+    for (int c = 0; c < nchunks; ++c) z += zpart[(int64_t)c * P + k];
+    out[k] = z;
+}
+
+// Block partials of |Ap - F|^2, then the one-block total into sc[S_WBRES].
+__global__ void __launch_bounds__(kPvThreads) wb_resid_kernel(int P, const double *Ap, const double *F, double *part) {
+    __shared__ double sh[33];
+    const int k = blockIdx.x * kPvThreads + threadIdx.x;
+    double d = 0.0;
+    if (k < P) { d = Ap[k] - F[k]; d *= d; }
+    d = pv_block_sum(d, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = d;
+}
+
+__global__ void __launch_bounds__(kPvThreads) wb_resid_total_kernel(int nb, const double *part, double *sc) {
+    __shared__ double sh[33];
+    const double v = pv_partials(part, nb, sh);
+    if (threadIdx.x == 0) sc[S_WBRES] = v;
+}
+
 __global__ void update_kernel(double *params, const double *x, int P, double lr) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) params[k] -= lr * x[k];
 }
@@ -329,6 +565,126 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     if (fnorm > 0.0 && resid > rtol) {
         *env.msg = "SR: conjugate gradient reached max_iter before the tolerance";
         return NQS_ERR_NOT_CONVERGED;
+    }
+    return NQS_OK;
+}
+
+size_t sr_woodbury_workspace_doubles(int64_t n, int P) {
+    // A [2n x 2n], column means [2P], ehat, b, t [2n], zpart [256][P], F, Ap, two scratch P-vectors,
+    // scalars, two block-partial arrays
+    const size_t m = 2 * (size_t)n;
+    return m * m + 2 * (size_t)P + 3 * m + 256 * (size_t)P + 4 * (size_t)P + S_COUNT +
+           2 * (size_t)((P + kPvThreads - 1) / kPvThreads);
+}
+
+int run_sr_woodbury(const Problem &pr, const double *O, const double *eloc, int64_t n, double eps, double lr,
+                    double *delta, double *params, int apply, double *ws, double *resid_out, double *energy_out,
+                    const LaunchEnv &env) {
+    const int P = pr.P;
+    const int64_t m = 2 * n;
+    const int T = (int)((m + kWb - 1) / kWb);
+    double *A = ws;
+    double *mu = A + (size_t)m * m;
+    double *ehat = mu + 2 * (size_t)P;
+    double *b = ehat + m;
+    double *t = b + m;
+    double *zpart = t + m;
+    double *F = zpart + (size_t)256 * P;
+    double *Ap = F + P;
+    double *tmp1 = Ap + P;
+    double *tmp2 = tmp1 + P;
+    double *sc = tmp2 + P;
+    const int pvb = (P + kPvThreads - 1) / kPvThreads;
+    double *part = sc + S_COUNT;
+    double *part2 = part + pvb;
+    cudaStream_t s = env.stream;
+    int64_t launches = 0;
+    const int nch_half = chunks_for(n, P, env.num_sms);
+    const int64_t chunk_half = (n + nch_half - 1) / nch_half;
+    const int nch = chunks_for(m, P, env.num_sms);
+    const int64_t chunk_rows = (m + nch - 1) / nch;
+    const int colb = (P + kColThreads - 1) / kColThreads;
+    const int sumb = (P + 255) / 256;
+    const int vecb = (int)std::min<int64_t>((m + 255) / 256, 4096);
+
+    // <E>, Ehat; b = Ehat / n; column means of each half of O
+    energy_kernel<<<1, kVecThreads, 0, s>>>(eloc, n, ehat, sc);
+    wb_rhs_kernel<<<vecb, 256, 0, s>>>(ehat, m, n, b, t);
+    gemv_cols_kernel<<<dim3(colb, nch_half), kColThreads, 0, s>>>(O, t, n, P, chunk_half, zpart, sc);
+    wb_chunk_sum_kernel<<<sumb, 256, 0, s>>>(zpart, nch_half, P, mu);
+    gemv_cols_kernel<<<dim3(colb, nch_half), kColThreads, 0, s>>>(O + (size_t)n * P, t, n, P, chunk_half, zpart, sc);
+    wb_chunk_sum_kernel<<<sumb, 256, 0, s>>>(zpart, nch_half, P, mu + P);
+    launches += 6;
+    // A = Ohat Ohat^T / n + eps I (lower tiles)
+    const int64_t tiles = (int64_t)T * (T + 1) / 2;
+    wb_tile_kernel<true><<<(unsigned)tiles, kWbThreads, 0, s>>>(O, P, P, mu, n, eps, A, m, 0);
+    ++launches;
+    // A = L L^T, blocked right-looking
+    for (int kb = 0; kb < T; ++kb) {
+        wb_potrf_kernel<<<1, kWbThreads, 0, s>>>(A, m, kb);
+        ++launches;
+        const int below = T - kb - 1;
+        if (below > 0) {
+            wb_trsm_kernel<<<below, kWb, 0, s>>>(A, m, kb);
+            const int64_t ut = (int64_t)below * (below + 1) / 2;
+            wb_tile_kernel<false><<<(unsigned)ut, kWbThreads, 0, s>>>(A, m, kWb, nullptr, n, 0.0, A, m, kb);
+            launches += 2;
+        }
+    }
+    // L z = b, then L^T y = z (in b)
+    for (int kb = 0; kb < T; ++kb) {
+        wb_fwd_diag_kernel<<<1, kWb, 0, s>>>(A, m, kb, b);
+        ++launches;
+        const int64_t rows_below = m - (int64_t)(kb + 1) * kWb;
+        if (rows_below > 0) {
+            wb_fwd_update_kernel<<<(unsigned)((rows_below + kRowWarps - 1) / kRowWarps), kRowWarps * 32, 0, s>>>(
+                A, m, kb, b);
+            ++launches;
+        }
+    }
+    for (int kb = T - 1; kb >= 0; --kb) {
+        wb_bwd_diag_kernel<<<1, kWb, 0, s>>>(A, m, kb, b);
+        ++launches;
+        if (kb > 0) {
+            wb_bwd_update_kernel<<<(unsigned)(((int64_t)kb * kWb + 255) / 256), 256, 0, s>>>(A, m, kb, b);
+            ++launches;
+        }
+    }
+    // delta = Ohat^T y = O^T (y minus its half means)
+    center_kernel<<<1, kVecThreads, 0, s>>>(b, n, sc);
+    gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, b, m, P, chunk_rows, zpart, sc);
+    wb_chunk_sum_kernel<<<sumb, 256, 0, s>>>(zpart, nch, P, delta);
+    launches += 3;
+    // residual of the parameter-space system: |(S + eps I) delta - F| / |F|
+    gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, ehat, m, P, chunk_rows, zpart, sc);
+    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch, P, n, tmp1, F, tmp2, part);
+    cg_init_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
+    // (S_DONE is set when F = 0; delta is then 0 and the kernels below skip)
+    gemv_rows_kernel<<<(unsigned)((m + kRowWarps - 1) / kRowWarps), kRowWarps * 32, 0, s>>>(O, delta, m, P, t, sc);
+    center_kernel<<<1, kVecThreads, 0, s>>>(t, n, sc);
+    gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, t, m, P, chunk_rows, zpart, sc);
+    cg_ap_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch, P, n, eps, delta, Ap, part2, sc);
+    wb_resid_kernel<<<pvb, kPvThreads, 0, s>>>(P, Ap, F, part);
+    wb_resid_total_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
+    launches += 9;
+    *env.launches += launches;
+    if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR (sample-space) launch failed"; return NQS_ERR_CUDA; }
+    double host_sc[S_COUNT];
+    cudaError_t e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { *env.msg = std::string("SR (sample-space): ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
+    const double fnorm = host_sc[S_FNORM];
+    const double resid = fnorm > 0.0 ? std::sqrt(host_sc[S_WBRES]) / fnorm : 0.0;
+    if (resid_out) *resid_out = resid;
+    if (energy_out) { energy_out[0] = host_sc[S_ERE]; energy_out[1] = host_sc[S_EIM]; }
+    if (!std::isfinite(resid) || !std::isfinite(host_sc[S_ERE])) {
+        *env.msg = "SR (sample-space): non-finite result (a Cholesky pivot was not positive)";
+        return NQS_ERR_NONFINITE;
+    }
+    if (apply) {
+        update_kernel<<<(P + 255) / 256, 256, 0, s>>>(params, delta, P, lr);
+        ++*env.launches;
+        if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR update launch failed"; return NQS_ERR_CUDA; }
     }
     return NQS_OK;
 }

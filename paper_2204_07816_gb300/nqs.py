@@ -26,7 +26,8 @@ MODEL = {'j1j2': 0, 'tj': 1}
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
-           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_set_sm_limit', 'nqs_sampler_counts')
+           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve',
+           'nqs_sr_solve_woodbury', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_set_sm_limit', 'nqs_sampler_counts')
 
 
 class nqs_problem(ctypes.Structure):
@@ -77,6 +78,7 @@ def load(path=LIB_PATH):
         'nqs_noalloc_last_error': (ctypes.c_char_p, []),
         'nqs_sr_solve': (ctypes.c_int, [P, P, P, I64, D, D, I32, D, P, ctypes.POINTER(I32), ctypes.POINTER(D),
                                         ctypes.POINTER(D), I32]),
+        'nqs_sr_solve_woodbury': (ctypes.c_int, [P, P, P, I64, D, D, P, ctypes.POINTER(D), ctypes.POINTER(D), I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -300,6 +302,22 @@ class Context:
         self._check(self.lib.nqs_logpsi_grad(self.ctx, self._configs(configs), n, _ptr(out, torch.float64, 'O_out'),
                                              _prec(precision)))
         return out
+
+    def sr_solve_woodbury(self, O, eloc, eps=1e-4, lr=0.02, apply_update=False, delta=None):
+        """nqs_sr_solve_woodbury: delta from the 2n x 2n sample-space system."""
+        n = eloc.shape[0]
+        if tuple(O.shape) != (2 * n, self.P):
+            raise ValueError('O must be [2n, P]')
+        if delta is None:
+            delta = torch.empty(self.P, dtype=torch.float64, device=self.device)
+        resid = ctypes.c_double()
+        energy = (ctypes.c_double * 2)()
+        self._check(self.lib.nqs_sr_solve_woodbury(self.ctx, _ptr(O, torch.float64, 'O'),
+                                                   _ptr(eloc, torch.float64, 'eloc'), n, eps, lr,
+                                                   _ptr(delta, torch.float64, 'delta'), ctypes.byref(resid),
+                                                   ctypes.cast(energy, ctypes.POINTER(ctypes.c_double)),
+                                                   int(bool(apply_update))))
+        return delta, {'resid': resid.value, 'energy': complex(energy[0], energy[1])}
 
     def sr_solve(self, O, eloc, eps=1e-4, rtol=1e-8, max_iter=10000, lr=0.02, apply_update=False, delta=None):
         n = eloc.shape[0]
