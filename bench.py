@@ -46,6 +46,8 @@ def parse():
                     help='profiling mode: only run --steps E_loc passes over S uniform random samples')
     ap.add_argument('--serve', type=int, default=0, metavar='R',
                     help='serving mode: R Poisson-arriving SR-step requests of mixed lattices (continuous batching)')
+    ap.add_argument('--sr-compare', action='store_true',
+                    help='time the CG and the sample-space (Woodbury) SR solves on the same O and E_loc')
     ap.add_argument('--serve-partition', action='store_true',
                     help='serving mode with per-class SM shares (default: every request sized for the whole GPU)')
     return ap.parse_args()
@@ -126,6 +128,70 @@ def profile_eloc(args):
     ctx.sync()
     print(json.dumps({'mode': 'profile-eloc', 'workload': args.workload, 'samples': args.profile_eloc,
                       'precision': args.precision, 'ms': times, 'samples_per_s': args.profile_eloc / (min(times) / 1e3)}))
+
+
+def sr_compare(args):
+    """CG (parameter space) against the sample-space Cholesky solve on the
+    same O and E_loc: time, CG iterations, and the difference of the deltas."""
+    import numpy as np
+    import torch
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300 import nqs
+    from paper_2204_07816_gb300.vmc import run_vmc
+    nbuild.build()
+    out = []
+
+    def timed(fn):
+        best, res = None, None
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best, res
+
+    def case(name, prob, params, n, cfg_source, eps=1e-4):
+        ctx = nqs.Context(prob, torch.tensor(params, dtype=torch.float64, device='cuda'), seed=5)
+        N = prob.L * prob.L
+        if cfg_source == 'sampled':
+            cfg, _ = ctx.sample(n // 4, 4, 1, 20, 'bf16')
+        else:
+            cfg = torch.from_numpy(nqs_synth.random_configs(N, prob.n_up, prob.n_down, n, seed=9)).cuda()
+        E = ctx.local_energy(cfg, None, 'bf16')
+        O = ctx.logpsi_grad(cfg, 'bf16')
+        t_cg, (d_cg, info) = timed(lambda: ctx.sr_solve(O, E, eps=eps, rtol=1e-8))
+        t_w0, (_, iw0) = timed(lambda: ctx.sr_solve_woodbury(O, E, eps=eps, refine_steps=0))
+        t_wb, (d_wb, iw) = timed(lambda: ctx.sr_solve_woodbury(O, E, eps=eps, refine_steps=1))
+        m, P = 2 * n, ctx.P
+        fl = 2.0 * m * m * P / 2 + m ** 3 / 3.0      # lower-triangle Gram + Cholesky (FLOP)
+        rel = float(torch.linalg.norm(d_cg - d_wb) / torch.linalg.norm(d_wb))
+        out.append({'case': name, 'P': P, 'samples': n, 'eps': eps, 'cg_ms': round(t_cg, 2), 'cg_iters': info['iters'],
+                    'cg_resid': info['resid'], 'woodbury_ms': round(t_wb, 2), 'woodbury_resid': iw['resid'],
+                    'woodbury_norefine_ms': round(t_w0, 2), 'woodbury_norefine_resid': iw0['resid'],
+                    'woodbury_fp64_tflops': round(fl / (t_w0 * 1e-3) / 1e12, 3), 'delta_rel_diff': rel})
+        ctx.close()
+
+    # 4x4 Heisenberg after 60 SR steps (the late-training spectrum that makes CG slow)
+    prob4 = nqs.make_problem('j1j2', 4, J1=1.0, J2=0.0, sign_rule=True, n_layers=3, channels=16)
+    p4 = nqs_synth.random_params(1, 16, 3, seed=61, scale=0.3)
+    p4, _ = run_vmc(prob4, p4, 60, 256, 4, burn_in=20, precision='bf16', eps=1e-3, lr=0.05, seed=62)
+    case('heisenberg_4x4_C16_after_60_steps', prob4, p4, 1024, 'sampled', eps=1e-3)
+    case('heisenberg_4x4_C16_after_60_steps', prob4, p4, 1024, 'sampled', eps=1e-4)
+    w = nqs_synth.WORKLOADS['j1j2_10x10']
+    prob10 = nqs.make_problem('j1j2', 10, J1=1.0, J2=0.5, n_layers=6, channels=16)
+    p10 = nqs_synth.random_params(1, 16, 6, seed=1)
+    for n in (256, 1024, 4096):
+        case('j1j2_10x10_C16_L6', prob10, p10, n, 'uniform')
+    prob16 = nqs.make_problem('j1j2', 16, J1=1.0, J2=0.5, n_layers=8, channels=32)
+    p16 = nqs_synth.random_params(1, 32, 8, seed=1)
+    for n in (256, 1024):
+        case('j1j2_16x16_C32_L8', prob16, p16, n, 'uniform')
+    print(json.dumps({'mode': 'sr-compare', 'cases': out, 'dtype': 'f64', 'data': 'synthetic'}), flush=True)
 
 
 def dense_forward_flops(w):
@@ -351,6 +417,9 @@ def main():
         return
     if args.serve:
         run_serve(args)
+        return
+    if args.sr_compare:
+        sr_compare(args)
         return
     # the oracle's process pool is started before the first GPU call
     rank = int(os.environ.get('RANK', '0'))

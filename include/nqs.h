@@ -281,12 +281,16 @@ int nqs_sr_solve(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, d
  * Work: (2n)^2 P + (2n)^3 / 3 multiply-adds, against 4 n P per CG
  * iteration, so it pays when CG needs more than about n / 2 iterations.
  * Arguments as nqs_sr_solve; eps must be > 0 and n <= 32,768 (workspace
- * (2n)^2 float64, owned by the context). resid_out (HOST) receives
- * ||(S + eps I) delta - F|| / ||F||, evaluated matrix-free after the solve.
- * Returns NQS_ERR_NONFINITE if a pivot was not positive or a value is not
- * finite; the update is then not applied. */
+ * (2n)^2 float64, owned by the context). refine_steps (0..8): steps of
+ * iterative refinement, each recomputing the sample-space residual
+ * Ehat / n - (Ohat Ohat^T / n + eps I) y from O (two passes over O) and
+ * solving for the correction with the same factor. resid_out (HOST)
+ * receives ||(S + eps I) delta - F|| / ||F||, evaluated matrix-free after
+ * the solve. Returns NQS_ERR_NONFINITE if a pivot was not positive or a
+ * value is not finite; the update is then not applied. */
 int nqs_sr_solve_woodbury(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, double eps, double lr,
-                          double *delta_out, double *resid_out, double *energy_out, int32_t apply_update);
+                          int32_t refine_steps, double *delta_out, double *resid_out, double *energy_out,
+                          int32_t apply_update);
 
 #ifdef __cplusplus
 }

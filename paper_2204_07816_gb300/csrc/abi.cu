@@ -479,17 +479,19 @@ int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, dou
 }
 
 int nqs_sr_solve_woodbury(nqs_ctx *c, const double *O, const double *eloc, int64_t n, double eps, double lr,
-                          double *delta, double *resid_out, double *energy_out, int32_t apply_update) {
+                          int32_t refine_steps, double *delta, double *resid_out, double *energy_out,
+                          int32_t apply_update) {
     if (int rc = check_ctx(c)) return rc;
     if (n <= 0 || !O || !eloc || !delta) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: bad arrays");
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: eps must be > 0");
     if (n > kWoodburyMaxSamples) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: n_s above the limit");
+    if (refine_steps < 0 || refine_steps > 8) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve_woodbury: refine_steps not in 0..8");
     if (int rc = ensure_scratch(c, sr_woodbury_workspace_doubles(n, c->p.P) * sizeof(double))) return rc;
     LaunchEnv env = env_of(c);
     env.num_sms = c->num_sms;
     double resid = 0.0, energy[2] = {0.0, 0.0};
-    const int rc = run_sr_woodbury(c->p, O, eloc, n, eps, lr, delta, c->params, apply_update, (double *)c->scratch,
-                                   &resid, energy, env);
+    const int rc = run_sr_woodbury(c->p, O, eloc, n, eps, lr, refine_steps, delta, c->params, apply_update,
+                                   (double *)c->scratch, &resid, energy, env);
     if (resid_out) *resid_out = resid;
     if (energy_out) { energy_out[0] = energy[0]; energy_out[1] = energy[1]; }
     return rc;

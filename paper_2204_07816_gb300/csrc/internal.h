@@ -94,7 +94,7 @@ int run_sr_solve(const Problem &p, const double *O, const double *eloc, int64_t 
 // sample-space (Woodbury) form: 2n x 2n Cholesky in place of CG
 size_t sr_woodbury_workspace_doubles(int64_t n, int P);
 int run_sr_woodbury(const Problem &p, const double *O, const double *eloc, int64_t n, double eps, double lr,
-                    double *delta, double *params, int apply, double *workspace, double *resid_out,
-                    double *energy_out, const LaunchEnv &env);
+                    int refine_steps, double *delta, double *params, int apply, double *workspace,
+                    double *resid_out, double *energy_out, const LaunchEnv &env);
 
 }  // namespace nqs

@@ -451,6 +451,22 @@ __global__ void wb_rhs_kernel(const double *v, int64_t m, int64_t n, double *b, 
     }
 }
 
+// Refinement right-hand side: r = Ehat / n - (Oc Oc^T y / n + eps y), with t = Oc Oc^T y.
+__global__ void wb_refine_rhs_kernel(const double *ehat, const double *t, const double *y, int64_t m, int64_t n,
+                                     double eps, double *r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = ehat[i] / (double)n - fma(eps, y[i], t[i] / (double)n);
+}
+
+// y += dy, and yc = y (to be centred).
+__global__ void wb_add_copy_kernel(double *y, const double *dy, int64_t m, double *yc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = dy ? y[i] + dy[i] : y[i];
+        y[i] = v;
+        yc[i] = v;
+    }
+}
+
 // out[k] = sum over chunks of zpart[c][k] (fixed order).
 __global__ void wb_chunk_sum_kernel(const double *zpart, int nchunks, int P, double *out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -570,16 +586,16 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
 }
 
 size_t sr_woodbury_workspace_doubles(int64_t n, int P) {
-    // A [2n x 2n], column means [2P], ehat, b, t [2n], zpart [256][P], F, Ap, two scratch P-vectors,
-    // scalars, two block-partial arrays
+    // A [2n x 2n], column means [2P], ehat, b, t, yc, r [2n], zpart [256][P], F, Ap, two scratch
+    // P-vectors, scalars, two block-partial arrays
     const size_t m = 2 * (size_t)n;
-    return m * m + 2 * (size_t)P + 3 * m + 256 * (size_t)P + 4 * (size_t)P + S_COUNT +
+    return m * m + 2 * (size_t)P + 5 * m + 256 * (size_t)P + 4 * (size_t)P + S_COUNT +
            2 * (size_t)((P + kPvThreads - 1) / kPvThreads);
 }
 
 int run_sr_woodbury(const Problem &pr, const double *O, const double *eloc, int64_t n, double eps, double lr,
-                    double *delta, double *params, int apply, double *ws, double *resid_out, double *energy_out,
-                    const LaunchEnv &env) {
+                    int refine_steps, double *delta, double *params, int apply, double *ws, double *resid_out,
+                    double *energy_out, const LaunchEnv &env) {
     const int P = pr.P;
     const int64_t m = 2 * n;
     const int T = (int)((m + kWb - 1) / kWb);
@@ -588,7 +604,9 @@ int run_sr_woodbury(const Problem &pr, const double *O, const double *eloc, int6
     double *ehat = mu + 2 * (size_t)P;
     double *b = ehat + m;
     double *t = b + m;
-    double *zpart = t + m;
+    double *yc = t + m;
+    double *r = yc + m;
+    double *zpart = r + m;
     double *F = zpart + (size_t)256 * P;
     double *Ap = F + P;
     double *tmp1 = Ap + P;
@@ -631,30 +649,48 @@ int run_sr_woodbury(const Problem &pr, const double *O, const double *eloc, int6
             launches += 2;
         }
     }
-    // L z = b, then L^T y = z (in b)
-    for (int kb = 0; kb < T; ++kb) {
-        wb_fwd_diag_kernel<<<1, kWb, 0, s>>>(A, m, kb, b);
-        ++launches;
-        const int64_t rows_below = m - (int64_t)(kb + 1) * kWb;
-        if (rows_below > 0) {
-            wb_fwd_update_kernel<<<(unsigned)((rows_below + kRowWarps - 1) / kRowWarps), kRowWarps * 32, 0, s>>>(
-                A, m, kb, b);
+    // L z = v, then L^T y = z (in place)
+    auto chol_solve = [&](double *v) {
+        for (int kb = 0; kb < T; ++kb) {
+            wb_fwd_diag_kernel<<<1, kWb, 0, s>>>(A, m, kb, v);
             ++launches;
+            const int64_t rows_below = m - (int64_t)(kb + 1) * kWb;
+            if (rows_below > 0) {
+                wb_fwd_update_kernel<<<(unsigned)((rows_below + kRowWarps - 1) / kRowWarps), kRowWarps * 32, 0,
+                                       s>>>(A, m, kb, v);
+                ++launches;
+            }
         }
-    }
-    for (int kb = T - 1; kb >= 0; --kb) {
-        wb_bwd_diag_kernel<<<1, kWb, 0, s>>>(A, m, kb, b);
-        ++launches;
-        if (kb > 0) {
-            wb_bwd_update_kernel<<<(unsigned)(((int64_t)kb * kWb + 255) / 256), 256, 0, s>>>(A, m, kb, b);
+        for (int kb = T - 1; kb >= 0; --kb) {
+            wb_bwd_diag_kernel<<<1, kWb, 0, s>>>(A, m, kb, v);
             ++launches;
+            if (kb > 0) {
+                wb_bwd_update_kernel<<<(unsigned)(((int64_t)kb * kWb + 255) / 256), 256, 0, s>>>(A, m, kb, v);
+                ++launches;
+            }
         }
+    };
+    // delta = Ohat^T y = O^T (y minus its half means); dy (nullable) is added to y first
+    auto delta_of = [&](const double *dy) {
+        wb_add_copy_kernel<<<vecb, 256, 0, s>>>(b, dy, m, yc);
+        center_kernel<<<1, kVecThreads, 0, s>>>(yc, n, sc);
+        gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, yc, m, P, chunk_rows, zpart, sc);
+        wb_chunk_sum_kernel<<<sumb, 256, 0, s>>>(zpart, nch, P, delta);
+        launches += 4;
+    };
+    chol_solve(b);
+    delta_of(nullptr);
+    // iterative refinement in the sample space: r = Ehat / n - A y with A y = Oc delta / n + eps y
+    // (evaluated from O, not from the factor), then y += A^-1 r
+    for (int it = 0; it < refine_steps; ++it) {
+        gemv_rows_kernel<<<(unsigned)((m + kRowWarps - 1) / kRowWarps), kRowWarps * 32, 0, s>>>(O, delta, m, P, t,
+                                                                                                sc);
+        center_kernel<<<1, kVecThreads, 0, s>>>(t, n, sc);
+        wb_refine_rhs_kernel<<<vecb, 256, 0, s>>>(ehat, t, b, m, n, eps, r);
+        launches += 3;
+        chol_solve(r);
+        delta_of(r);
     }
-    // delta = Ohat^T y = O^T (y minus its half means)
-    center_kernel<<<1, kVecThreads, 0, s>>>(b, n, sc);
-    gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, b, m, P, chunk_rows, zpart, sc);
-    wb_chunk_sum_kernel<<<sumb, 256, 0, s>>>(zpart, nch, P, delta);
-    launches += 3;
     // residual of the parameter-space system: |(S + eps I) delta - F| / |F|
     gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, ehat, m, P, chunk_rows, zpart, sc);
     cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch, P, n, tmp1, F, tmp2, part);

@@ -78,7 +78,8 @@ def load(path=LIB_PATH):
         'nqs_noalloc_last_error': (ctypes.c_char_p, []),
         'nqs_sr_solve': (ctypes.c_int, [P, P, P, I64, D, D, I32, D, P, ctypes.POINTER(I32), ctypes.POINTER(D),
                                         ctypes.POINTER(D), I32]),
-        'nqs_sr_solve_woodbury': (ctypes.c_int, [P, P, P, I64, D, D, P, ctypes.POINTER(D), ctypes.POINTER(D), I32]),
+        'nqs_sr_solve_woodbury': (ctypes.c_int, [P, P, P, I64, D, D, I32, P, ctypes.POINTER(D), ctypes.POINTER(D),
+                                                 I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -303,7 +304,7 @@ class Context:
                                              _prec(precision)))
         return out
 
-    def sr_solve_woodbury(self, O, eloc, eps=1e-4, lr=0.02, apply_update=False, delta=None):
+    def sr_solve_woodbury(self, O, eloc, eps=1e-4, lr=0.02, apply_update=False, delta=None, refine_steps=0):
         """nqs_sr_solve_woodbury: delta from the 2n x 2n sample-space system."""
         n = eloc.shape[0]
         if tuple(O.shape) != (2 * n, self.P):
@@ -314,7 +315,8 @@ class Context:
         energy = (ctypes.c_double * 2)()
         self._check(self.lib.nqs_sr_solve_woodbury(self.ctx, _ptr(O, torch.float64, 'O'),
                                                    _ptr(eloc, torch.float64, 'eloc'), n, eps, lr,
-                                                   _ptr(delta, torch.float64, 'delta'), ctypes.byref(resid),
+                                                   int(refine_steps), _ptr(delta, torch.float64, 'delta'),
+                                                   ctypes.byref(resid),
                                                    ctypes.cast(energy, ctypes.POINTER(ctypes.c_double)),
                                                    int(bool(apply_update))))
         return delta, {'resid': resid.value, 'energy': complex(energy[0], energy[1])}
