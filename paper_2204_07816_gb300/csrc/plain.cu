@@ -188,7 +188,7 @@ __global__ void init_chains_kernel(Problem p, uint64_t seed, int n_chains, int8_
 }
 
 struct SampleSmem {
-    size_t cur, spins, pi, pj, pu, ca, cphi, list, total;
+    size_t cur, spins, pi, pj, pu, ca, cphi, list, cnt, total;
 };
 
 __host__ __device__ inline SampleSmem sample_smem(const Problem &p, size_t base, int G) {
@@ -202,6 +202,7 @@ __host__ __device__ inline SampleSmem sample_smem(const Problem &p, size_t base,
     e.ca = o; o = align16(o + 8 * (size_t)G);
     e.cphi = o; o = align16(o + 8 * (size_t)G);
     e.list = o; o = align16(o + 4 * (size_t)(G + 1));
+    e.cnt = o; o = align16(o + 16);   // moves, accepted moves of the block (kept out of registers)
     e.total = o;
     return e;
 }
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
     double *ca = reinterpret_cast<double *>(smem + ss.ca);
     double *cphi = reinterpret_cast<double *>(smem + ss.cphi);
     int *list = reinterpret_cast<int *>(smem + ss.list);
+    unsigned long long *scnt = reinterpret_cast<unsigned long long *>(smem + ss.cnt);
 
     const int c0 = blockIdx.x * G;
     if (c0 >= n_chains) return;
@@ -241,10 +243,10 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
     __syncthreads();
     plain_forward<T, CB>(p, params, p64, cur, gc, net);
     for (int g = threadIdx.x; g < gc; g += blockDim.x) { ca[g] = net.a[g]; cphi[g] = net.phi[g]; }
+    if (threadIdx.x == 0) { scnt[0] = 0; scnt[1] = 0; }
     __syncthreads();
 
     const int n_sweeps = burn_in + spc * sweeps_between;
-    unsigned long long n_moves = 0, n_acc = 0;
     for (int sweep = 0; sweep < n_sweeps; ++sweep) {
         for (int q = 0; q < N; ++q) {
             const uint64_t step = step0 + (uint64_t)sweep * N + q;
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
                 for (int g = 0; g < gc; ++g)
                     if (cur[g * N + pi[g]] != cur[g * N + pj[g]]) list[cnt++] = g;
                 list[G] = cnt;
+                scnt[0] += (unsigned long long)cnt;
             }
             __syncthreads();
             const int cnt = list[G];
@@ -279,9 +282,8 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
                 for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
                     const int g = list[m];
                     const double delta = 2.0 * (net.a[m] - ca[g]);
-                    ++n_moves;
                     if (delta >= 0.0 || pu[g] < exp(delta)) {
-                        ++n_acc;
+                        atomicAdd(&scnt[1], 1ull);
                         const int i = pi[g], j = pj[g];
                         const int8_t t = cur[g * N + i];
                         cur[g * N + i] = cur[g * N + j];
@@ -308,9 +310,10 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
         }
     }
     for (int r = threadIdx.x; r < gc * N; r += blockDim.x) chains[(size_t)c0 * N + r] = cur[r];
-    if (moves && n_moves) {
-        atomicAdd(&moves[0], n_moves);
-        atomicAdd(&moves[1], n_acc);
+    __syncthreads();
+    if (threadIdx.x == 0 && moves && scnt[0]) {
+        atomicAdd(&moves[0], scnt[0]);
+        atomicAdd(&moves[1], scnt[1]);
     }
 }
 

@@ -868,10 +868,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     double *wlu = cphi + per_block;
     int *wpi = reinterpret_cast<int *>(wlu + kPropWindow * per_block);
     int *wpj = wpi + kPropWindow * per_block;
+    // moves and accepted moves of the block, in shared memory after the proposal window (not live in
+    // registers across the forward; the address is recomputed where it is used)
+    auto scnt = [&]() {
+        return reinterpret_cast<unsigned long long *>(smem + pl.o_extra +
+                                                      ((al16(per_block * pl.N) + al16(8 * pl.slots * (pl.G + 1)) +
+                                                        16 * per_block + 16 * kPropWindow * per_block + 7) & ~7u));
+    };
+    if (threadIdx.x == 0) { scnt()[0] = 0; scnt()[1] = 0; }
     // chain groups: group k = blockIdx.x + j * gridDim.x (one pass when the
     // grid covers every group; fewer blocks when the launch is held to an SM share)
     bool ok = true;
-    unsigned long long n_moves = 0, n_acc = 0;
     for (int c0 = blockIdx.x * per_block; ok && c0 < n_chains; c0 += gridDim.x * per_block) {
     const int gc = min(per_block, n_chains - c0);
     {
@@ -925,6 +932,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
             int total = 0;
             for (int s = 0; s < S; ++s) total += list[s * (G + 1) + G];
             if (total == 0) continue;
+            if (threadIdx.x == 0) scnt()[0] += (unsigned long long)total;
             for (int r = threadIdx.x; r < per_block * N; r += blockDim.x) {
                 const int slot_row = r / N, site = r - slot_row * N;
                 const int s = slot_row / G, m = slot_row - s * G;
@@ -942,10 +950,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
                 const int c = list[s * (G + 1) + m];
                 const double an = sh.res[s * 2 * G + m];
                 const double delta = 2.0 * (an - ca[c]);
-                ++n_moves;
                 // u < exp(2 (a' - a)) evaluated as log u < 2 (a' - a), log u drawn with the proposal
                 if (delta >= 0.0 || wlu[w * per_block + c] < delta) {
-                    ++n_acc;
+                    atomicAdd(&scnt()[1], 1ull);
                     const int i = pi_s[c], j = pj_s[c];
                     const int8_t t = cur[c * N + i];
                     cur[c * N + i] = cur[c * N + j];
@@ -974,9 +981,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
         for (int r = threadIdx.x; r < gc * N; r += blockDim.x) chains[(size_t)c0 * N + r] = cur[r];
     __syncthreads();
     }
-    if (moves && n_moves) {
-        atomicAdd(&moves[0], n_moves);
-        atomicAdd(&moves[1], n_acc);
+    __syncthreads();
+    if (threadIdx.x == 0 && moves && scnt()[0]) {
+        atomicAdd(&moves[0], scnt()[0]);
+        atomicAdd(&moves[1], scnt()[1]);
     }
     tc_teardown(pl, sh, st);
 }
@@ -1086,7 +1094,7 @@ int eloc_extra(const Problem &p) {
 
 int sample_extra(const Problem &p, int G, int slots) {
     const int per = G * slots;
-    return (int)(al16(per * p.N) + al16(4 * 2 * (slots * (G + 1))) + 16 * per + 16 * kPropWindow * per);
+    return (int)(al16(per * p.N) + al16(4 * 2 * (slots * (G + 1))) + 16 * per + 16 * kPropWindow * per + 24);
 }
 
 // Relative throughput of a one-slot plan: useful rows per computed row,
