@@ -190,13 +190,34 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
                 for (int k = 0; k < 9; ++k) { a0[k] = 0.f; a1[k] = 0.f; }
                 const float *g0 = gz + o * NP, *g1 = gz + (C + o) * NP;
                 const float *hc = hprev + c * NP;
-                for (int s = 0; s < N; ++s) {
-                    const float x0 = g0[s], x1 = g1[s];
+                // sites in row-major order with the 3 x 3 input window held in registers: moving one site
+                // along x reuses six of its values and loads the three of the new column
+                for (int y = 0; y < L; ++y) {
+                    const int rb[3] = {((y + L - 1) % L) * L, y * L, ((y + 1) % L) * L};
+                    float win[3][3];
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        const float hv = hc[nbr[k * N + s]];
-                        a0[k] = fmaf(x0, hv, a0[k]);
-                        a1[k] = fmaf(x1, hv, a1[k]);
+                    for (int dy = 0; dy < 3; ++dy) {
+                        win[dy][0] = hc[rb[dy] + L - 1];
+                        win[dy][1] = hc[rb[dy]];
+                        win[dy][2] = hc[rb[dy] + (L > 1 ? 1 : 0)];
+                    }
+                    for (int x = 0; x < L; ++x) {
+                        const int s = y * L + x;
+                        const float x0 = g0[s], x1 = g1[s];
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx) {
+                                a0[3 * dy + dx] = fmaf(x0, win[dy][dx], a0[3 * dy + dx]);
+                                a1[3 * dy + dx] = fmaf(x1, win[dy][dx], a1[3 * dy + dx]);
+                            }
+                        const int xn = x + 2 < L ? x + 2 : x + 2 - L;
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            win[dy][0] = win[dy][1];
+                            win[dy][1] = win[dy][2];
+                            win[dy][2] = hc[rb[dy] + xn];
+                        }
                     }
                 }
 #pragma unroll
