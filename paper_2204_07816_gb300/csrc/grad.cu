@@ -94,17 +94,21 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
             for (int e = threadIdx.x; e < C; e += blockDim.x) w[9 * cin * C + e] = prm[off + 9 * cin * C + e];
             __syncthreads();
             float *hout = gz;   // [C][NP]
-            for (int s = threadIdx.x; s < N; s += blockDim.x) {
-                float acc[C];
+            // one work item per (site, half of the output channels): twice the threads of one item per
+            // site on lattices with 2 N <= 256 sites, the same sums in the same order
+            constexpr int CH = C / 2;
+            for (int it = threadIdx.x; it < 2 * N; it += blockDim.x) {
+                const int half = it >= N, s = it - half * N;
+                float acc[CH];
 #pragma unroll
-                for (int o = 0; o < C; ++o) acc[o] = w[9 * cin * C + o];
+                for (int o = 0; o < CH; ++o) acc[o] = w[9 * cin * C + half * CH + o];
                 for (int k = 0; k < 9; ++k) {
                     const int sn = nbr[k * N + s];
                     for (int c = 0; c < cin; ++c) {
                         const float hv = hprev[c * NP + sn];
-                        const float4 *wr = reinterpret_cast<const float4 *>(w + (k * cin + c) * C);
+                        const float4 *wr = reinterpret_cast<const float4 *>(w + (k * cin + c) * C + half * CH);
 #pragma unroll
-                        for (int q = 0; q < C / 4; ++q) {
+                        for (int q = 0; q < CH / 4; ++q) {
                             const float4 wv = wr[q];
                             acc[4 * q] = fmaf(wv.x, hv, acc[4 * q]);
                             acc[4 * q + 1] = fmaf(wv.y, hv, acc[4 * q + 1]);
@@ -115,9 +119,10 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
                 }
                 float *Hl = Hs + (size_t)l * C * N, *Sl = Ss + (size_t)l * C * N;
 #pragma unroll
-                for (int o = 0; o < C; ++o) {
-                    const float sg = 1.0f / (1.0f + expf(-acc[o]));
-                    const float h = acc[o] * sg;
+                for (int oo = 0; oo < CH; ++oo) {
+                    const int o = half * CH + oo;
+                    const float sg = 1.0f / (1.0f + expf(-acc[oo]));
+                    const float h = acc[oo] * sg;
                     hout[o * NP + s] = h;
                     Hl[o * N + s] = h;
                     Sl[o * N + s] = sg;
