@@ -46,6 +46,10 @@ def parse():
                     help='profiling mode: only run --steps E_loc passes over S uniform random samples')
     ap.add_argument('--serve', type=int, default=0, metavar='R',
                     help='serving mode: R Poisson-arriving SR-step requests of mixed lattices (continuous batching)')
+    ap.add_argument('--profile-sample', type=int, default=0, metavar='CHAINS',
+                    help='small sampler-only run for profilers: CHAINS chains, 2 samples each')
+    ap.add_argument('--profile-grad', type=int, default=0, metavar='S',
+                    help='small O_k-only run for profilers: S uniform random samples')
     ap.add_argument('--sr-compare', action='store_true',
                     help='time the CG and the sample-space (Woodbury) SR solves on the same O and E_loc')
     ap.add_argument('--serve-partition', action='store_true',
@@ -192,6 +196,43 @@ def sr_compare(args):
     for n in (256, 1024):
         case('j1j2_16x16_C32_L8', prob16, p16, n, 'uniform')
     print(json.dumps({'mode': 'sr-compare', 'cases': out, 'dtype': 'f64', 'data': 'synthetic'}), flush=True)
+
+
+def profile_stage(args):
+    """Small sampler-only or O_k-only run for profilers (bf16 path of the workload)."""
+    import torch
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300 import nqs
+    nbuild.build()
+    w = nqs_synth.WORKLOADS[args.workload]
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    prob = (nqs.make_problem('j1j2', w['L'], J1=w['J1'], J2=w['J2'], n_layers=w['n_layers'], channels=w['channels'])
+            if w['model'] == 'j1j2' else
+            nqs.make_problem('tj', w['L'], t=w['t'], J=w['J'], n_up=w['n_up'], n_down=w['n_down'],
+                             n_layers=w['n_layers'], channels=w['channels']))
+    ctx = nqs.Context(prob, torch.tensor(params, dtype=torch.float64, device='cuda'), seed=1)
+    if args.profile_sample:
+        ctx.sample(args.profile_sample, 1, 1, 5, args.precision)      # burn-in outside the timed launches
+    else:
+        cfg = torch.from_numpy(nqs_synth.random_configs(w['L'] ** 2, w['n_up'], w['n_down'], args.profile_grad,
+                                                        3)).cuda()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if args.profile_sample:
+            ctx.sample(args.profile_sample, 2, 1, 0, args.precision)
+        else:
+            ctx.logpsi_grad(cfg, args.precision)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.sync()
+    print(json.dumps({'mode': 'profile-sample' if args.profile_sample else 'profile-grad', 'workload': args.workload,
+                      'chains' if args.profile_sample else 'samples': args.profile_sample or args.profile_grad,
+                      'precision': args.precision, 'ms': times}))
 
 
 def dense_forward_flops(w):
@@ -414,6 +455,9 @@ def main():
         return
     if args.profile_eloc:
         profile_eloc(args)
+        return
+    if args.profile_sample or args.profile_grad:
+        profile_stage(args)
         return
     if args.serve:
         run_serve(args)

@@ -252,8 +252,14 @@ __device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot, const
                     const uint32_t b = s > 0 ? one : minus_one;
                     w[o >> 1] |= b << (16 * (o & 1));
                 } else {
-                    const int k = 3 * o + (s == 0 ? 0 : (s == 1 ? 1 : 2));
-                    w[k >> 1] |= one << (16 * (k & 1));
+                    // one-hot channel (hole, up, down) = column 3 o + channel; every index is a
+                    // compile-time constant, so w stays in registers
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const int k = 3 * o + ch;
+                        const bool hit = ch == 0 ? s == 0 : (ch == 1 ? s == 1 : s == -1);
+                        if (hit) w[k >> 1] |= one << (16 * (k & 1));
+                    }
                 }
             }
         }
