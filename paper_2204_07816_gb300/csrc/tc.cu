@@ -428,8 +428,12 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
                 ca = fmaf(wa[c], hv, ca);
                 cp = fmaf(wa[C + c], hv, cp);
             }
-            contrib[2 * main] = ca;       // indexed by the row p * G + g
-            contrib[2 * main + 1] = cp;
+            // configuration-major ([a | phi][g][padded position p], row = p * G + g), so that the head's
+            // reads of one configuration's sites are consecutive words
+            const uint32_t pos = main / (uint32_t)pl.G, g = main - pos * (uint32_t)pl.G;
+            const uint32_t idx = g * (uint32_t)Lp2 + pos;
+            contrib[idx] = ca;
+            contrib[(uint32_t)(pl.G * Lp2) + idx] = cp;
         }
     }
     if (!ok) raise_abort(sh, err);
@@ -443,7 +447,7 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
 
 // a[g] = sum over sites of the head contributions (one warp per g, fixed order).
 __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const int *roll) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G, Lp2 = pl.Lp * pl.Lp;
     const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act +
                                                            (uint32_t)(slot * 2 + ((pl.n_layers - 1) & 1)) * pl.act_bytes);
     double *res = sh.res + slot * 2 * G;
@@ -457,9 +461,9 @@ __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const 
                 const int y = site / pl.L, x = site - y * pl.L;
                 cs = ((y - rg + pl.L) % pl.L) * pl.L + x;
             }
-            const int row = (int)(sh.sitetab[cs].x & 0xFFFFu) * G + g;
-            sa += contrib[2 * row];
-            sp += contrib[2 * row + 1];
+            const int idx = g * Lp2 + (int)(sh.sitetab[cs].x & 0xFFFFu);
+            sa += contrib[idx];
+            sp += contrib[G * Lp2 + idx];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
