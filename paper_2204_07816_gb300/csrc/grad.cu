@@ -296,19 +296,15 @@ int launch_grad_fast(const Problem &p, const float *p32, const double *p64, cons
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>(n, (int64_t)env.num_sms * grad_fast_blocks_per_sm(p)),
                              (int64_t)(scratch_bytes / (per_block * sizeof(float)))));
-    cudaError_t e;
-    if (p.C == 16) {
-        e = cudaFuncSetAttribute(grad_fast_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gl.total);
-        if (e == cudaSuccess)
-            grad_fast_kernel<16><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, O,
-                                                                                 (float *)scratch, per_block);
-    } else {
-        e = cudaFuncSetAttribute(grad_fast_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gl.total);
-        if (e == cudaSuccess)
-            grad_fast_kernel<32><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, O,
-                                                                                 (float *)scratch, per_block);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
+    if (int rc = allow_dynamic_smem(p.C == 16 ? grad_fast_kernel<16> : grad_fast_kernel<32>, gl.total, env))
+        return rc;
+    if (p.C == 16)
+        grad_fast_kernel<16><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, O,
+                                                                             (float *)scratch, per_block);
+    else
+        grad_fast_kernel<32><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, O,
+                                                                             (float *)scratch, per_block);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *env.msg = std::string("grad_fast_kernel: ") + cudaGetErrorString(e);
         return NQS_ERR_CUDA;

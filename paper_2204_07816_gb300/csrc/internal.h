@@ -21,6 +21,30 @@ struct LaunchEnv {
     std::string *msg;    // host error text
 };
 
+// Let a kernel use all the dynamic shared memory the device allows it (the opt-in maximum less the kernel's
+// static shared memory). The limit is a per-function attribute shared by every host thread, so it is set to this
+// fixed value and never to one launch's size: a context on another thread launching the same kernel with a
+// smaller size cannot lower it below this launch's need. need: this launch's dynamic bytes.
+template <typename K>
+inline int allow_dynamic_smem(K kernel, size_t need, const LaunchEnv &env) {
+    cudaFuncAttributes a{};
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e == cudaSuccess) {
+        const size_t cap = env.max_smem > a.sharedSizeBytes ? env.max_smem - a.sharedSizeBytes : 0;
+        if (need > cap) {
+            *env.msg = "launch needs " + std::to_string(need) + " bytes of dynamic shared memory (max " +
+                       std::to_string(cap) + ")";
+            return NQS_ERR_UNSUPPORTED;
+        }
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    }
+    if (e != cudaSuccess) {
+        *env.msg = std::string("kernel shared-memory attribute: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    return NQS_OK;
+}
+
 // Parameters converted for a precision: T = float copies of the layer
 // weights (FP32 path) or the packed bf16 operand images (tensor-core path).
 struct DeviceParams {

@@ -475,12 +475,7 @@ static int set_smem(K kernel, size_t bytes, const LaunchEnv &env) {
                    std::to_string(env.max_smem) + ")";
         return NQS_ERR_UNSUPPORTED;
     }
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) {
-        *env.msg = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
-        return NQS_ERR_CUDA;
-    }
-    return NQS_OK;
+    return allow_dynamic_smem(kernel, bytes, env);
 }
 
 template <typename T>

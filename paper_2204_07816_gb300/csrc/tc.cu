@@ -1175,12 +1175,7 @@ int check(const LaunchEnv &env, const char *what) {
 
 template <typename K>
 int prep(K kernel, const TcPlan &pl, const LaunchEnv &env) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.total);
-    if (e != cudaSuccess) {
-        *env.msg = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
-        return NQS_ERR_CUDA;
-    }
-    return NQS_OK;
+    return allow_dynamic_smem(kernel, pl.total, env);
 }
 
 }  // namespace
@@ -1311,8 +1306,7 @@ int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, i
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, cap));
     NQS_TC_DISPATCH(C, {
         auto k = eloc_tc_multi_kernel<CC>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) { *env.msg = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
+        if (int rc = allow_dynamic_smem(k, smem, env)) return rc;
         k<<<grid, kTcThreads, smem, env.stream>>>(dreqs, count, total, cols, counter, env.err);
     });
     return check(env, "eloc_tc_multi_kernel");

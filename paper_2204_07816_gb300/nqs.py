@@ -262,10 +262,15 @@ class Context:
                                               n, _ptr(out, torch.float64, 'out'), _prec(precision)))
         return out
 
-    def sample(self, n_chains, samples_per_chain, sweeps_between=1, burn_in=10, precision='fp64'):
+    def sample(self, n_chains, samples_per_chain, sweeps_between=1, burn_in=10, precision='fp64', out=None,
+               logpsi_out=None):
+        """nqs_sample; out / logpsi_out: optional contiguous [n, N] int8 and [n, 2] float64 device tensors
+        (for instance row slices of a larger buffer) that receive the samples."""
         n = n_chains * samples_per_chain
-        cfg = torch.empty((n, self.N), dtype=torch.int8, device=self.device)
-        lp = torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        cfg = out if out is not None else torch.empty((n, self.N), dtype=torch.int8, device=self.device)
+        lp = logpsi_out if logpsi_out is not None else torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        if tuple(cfg.shape) != (n, self.N) or tuple(lp.shape) != (n, 2):
+            raise ValueError('out must be [%d, %d] and logpsi_out [%d, 2]' % (n, self.N, n))
         self._check(self.lib.nqs_sample(self.ctx, n_chains, samples_per_chain, sweeps_between, burn_in,
                                         _ptr(cfg, torch.int8, 'configs_out'), _ptr(lp, torch.float64, 'logpsi_out'),
                                         _prec(precision)))

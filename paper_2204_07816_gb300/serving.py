@@ -18,7 +18,12 @@ runs its own loop of SR steps in a host thread:
   3. local derivatives and the SR solve on its stream.
 
 A request that arrives while others run is admitted as soon as memory is
-returned by a finished one and joins the next grouped launch.
+returned by a finished one and joins the next grouped launch. Sampling is
+issued as one launch per sample of every chain (the chains continue from
+launch to launch, so the samples are those of one launch), and requests on
+lattices up to 16 x 16 use high-priority streams: a large request's sampler
+no longer holds every SM for the seconds of a whole step while a small
+request waits to start.
 
 Optional SM shares (`partition_sms=True`, `_Partition`): while requests of
 both size classes run, the large class (lattices above 16 x 16) is held to
@@ -27,8 +32,8 @@ the budget is split evenly (at least 4 SMs a request), and a class running
 alone gets the whole GPU. Every launch of a request is then sized for its
 share (nqs_set_sm_limit; results do not change), and the grouped E_loc
 launches of a class are capped at the class budget. On the measured mix
-(up to 36 x 36) the shares made every step slower (p50 5.1 s against 1.9 s
-shared): the large requests' sampler and backward, held to fewer blocks,
+(up to 36 x 36) the shares made every step slower (p50 5.2-5.7 s against
+1.6-2.3 s shared): the large requests' sampler and backward, held to fewer blocks,
 keep their SMs proportionally longer, and the hardware scheduler already
 interleaves the streams; sharing the whole GPU is the default. Every kernel
 reduces in a fixed order and per-configuration results do not depend on
@@ -165,7 +170,9 @@ class _Run:
         self.req = req
         self.precision = precision
         self.sr_args = sr_args
-        self.stream = torch.cuda.Stream(device)
+        # lattices up to 16 x 16 run on high-priority streams: when a block of a large request's launch
+        # retires, the block scheduler starts the small requests' pending blocks first
+        self.stream = torch.cuda.Stream(device, priority=-1 if req.L * req.L <= _Batcher.SMALL_SITES else 0)
         self.device = device
         with torch.cuda.stream(self.stream):
             if req.params is None:
@@ -175,6 +182,9 @@ class _Run:
             self.eloc = torch.empty((req.n_samples, 2), dtype=torch.float64, device=device)
             self.O = torch.empty((2 * req.n_samples, self.ctx.P), dtype=torch.float64, device=device)
             self.delta = torch.empty(self.ctx.P, dtype=torch.float64, device=device)
+            n_s = req.n_chains * (req.n_samples // req.n_chains)
+            self.cfg_buf = torch.empty((n_s, req.L * req.L), dtype=torch.int8, device=device)
+            self.lp_buf = torch.empty((n_s, 2), dtype=torch.float64, device=device)
         self.spc = req.n_samples // req.n_chains
         self.result = RequestResult(req.rid)
         self.sampled = torch.cuda.Event()
@@ -191,8 +201,14 @@ class _Run:
                 if partition is not None:
                     self.ctx.set_sm_limit(partition.limit(self.req.rid))
                 with torch.cuda.stream(self.stream):
-                    self.cfg, _ = self.ctx.sample(self.req.n_chains, self.spc, 1,
-                                                  self.req.burn_in if step == 0 else 0, self.precision)
+                    # one launch per sample of every chain (burn-in in the first): no request holds the SMs
+                    # with a sampler launch of many sweeps while others wait to start theirs
+                    nc = self.req.n_chains
+                    for k in range(self.spc):
+                        self.ctx.sample(nc, 1, 1, self.req.burn_in if (step == 0 and k == 0) else 0,
+                                        self.precision, out=self.cfg_buf[k * nc:(k + 1) * nc],
+                                        logpsi_out=self.lp_buf[k * nc:(k + 1) * nc])
+                    self.cfg = self.cfg_buf
                 self.sampled.record(self.stream)
                 self.ready.clear()
                 batcher.submit(self)
@@ -216,7 +232,7 @@ class _Run:
 
     def close(self):
         self.ctx.close()
-        del self.O, self.eloc, self.delta, self.cfg
+        del self.O, self.eloc, self.delta, self.cfg, self.cfg_buf, self.lp_buf
 
 
 class _Batcher:
