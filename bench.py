@@ -407,7 +407,7 @@ def host_cores():
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the machine's host cores, each step a
+    """The reference arm: the FP64 oracle on this machine's host cores, each step a
     bounded sample of the same workload's E_loc."""
     rank = int(os.environ.get('RANK', '0'))
     if rank != 0:
