@@ -618,6 +618,14 @@ def main():
                     'flops': 'cone form (changed sites only) %.4g per launch' % flops,
                     'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,
                                    'frac': flops_dense / eloc_launch_s / 1e12 / peak}}
+            if w['channels'] == 16:
+                # context: the rate of back-to-back M128 N16 K16 MMAs (39.1 cycles each, bound by the shared-memory
+                # operand path; measured by paper_2204_07816_gb300/microbench/mma_rate.cu) at the clock seen: the
+                # ceiling of one MMA per 3x3 tap with 16 channels
+                mhz = (clocks or {}).get('sm_mhz') or peaks.get('sm_max_mhz', 2070.0)
+                n16 = 152 * (2.0 * 128 * 16 * 16 / 39.1) * mhz * 1e6 / 1e12
+                roof['mma_n16_ceiling'] = {'peak': n16, 'frac': achieved / n16,
+                                           'dense_form_frac': flops_dense / eloc_launch_s / 1e12 / n16}
         else:
             mhz = (clocks or {}).get('sm_mhz') or peaks.get('sm_max_mhz', 2070.0)
             lanes = 128 if args.precision == 'fp32' else 2
