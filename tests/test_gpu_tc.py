@@ -167,6 +167,38 @@ def test_sampler_bf16_chi_square():
     assert stats.chi2.sf(chi2, used.size - 1) > 1e-3
 
 
+def test_sampler_bf16_chi_square_tj():
+    """bf16 sampler on a t-J 4x4 sector (2 up, 2 down, 12 holes: 10,920
+    states; 16 channels) against the oracle's enumerated |psi|^2."""
+    from scipy import stats
+    w = WL['tj_12x12']
+    over = {'L': 4, 'n_up': 2, 'n_down': 2, 'channels': 16, 'n_layers': 2}
+    ctx, params = make_ctx(w, seed=15, param_seed=25, scale=1.5, **over)
+    spec, _ = oracle_of(w, **over)
+    basis = ed.sector_basis(16, 2, 2)
+    a, _ = cnn.forward(params, basis, spec)
+    p = np.exp(2 * (a - a.max()))
+    p /= p.sum()
+    assert p.max() / p.min() > 100.0
+    n_ch = 4096
+    cfg, _ = ctx.sample(n_ch, 1, 1, 40, 'bf16')
+    samples = cfg.cpu().numpy()
+    assert np.all((samples == 1).sum(1) == 2) and np.all((samples == -1).sum(1) == 2)
+    keys = ed.config_keys(basis)
+    idx = np.searchsorted(keys, ed.config_keys(samples))
+    assert np.all(keys[idx] == ed.config_keys(samples))
+    order = np.argsort(p)
+    cum = np.cumsum(p[order])
+    bins = np.empty(p.size, dtype=int)
+    bins[order] = np.minimum((cum * 32).astype(int), 31)
+    used = np.unique(bins)
+    bins = np.searchsorted(used, bins)
+    exp_c = np.bincount(bins, weights=p, minlength=used.size) * n_ch
+    obs = np.bincount(bins[idx], minlength=used.size)
+    chi2 = ((obs - exp_c) ** 2 / exp_c).sum()
+    assert stats.chi2.sf(chi2, used.size - 1) > 1e-3
+
+
 def test_sampler_bf16_conserves_sector_tj():
     w = WL['tj_12x12']
     ctx, _ = make_ctx(w, seed=6)

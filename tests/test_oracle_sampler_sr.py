@@ -131,6 +131,31 @@ def test_sampler_chi_square_against_enumeration(exact_4x4, seed):
     assert stats.chi2.sf(chi2_q, len(obs) - 1) < 1e-6
 
 
+def test_sampler_chi_square_tj_sector():
+    """t-J 4x4 with 2 up, 2 down and 12 holes (10,920 states): hops and
+    exchanges sample the enumerated |psi|^2, and the same counts reject
+    |psi|^1."""
+    spec = cnn.NetSpec(4, 3, 4, 2)
+    params = nqs_synth.random_params(3, 4, 2, seed=24, scale=2.0)
+    basis = ed.sector_basis(16, 2, 2)
+    assert basis.shape[0] == 10920
+    a, _ = cnn.forward(params, basis, spec)
+    p = np.exp(2 * (a - a.max()))
+    p /= p.sum()
+    assert p.max() / p.min() > 100.0
+    n_ch = 4096
+    ch0 = sampler.init_chains(4, n_ch, sampler.canonical_values(16, 2, 2))
+    samples = sampler.metropolis(params, spec, ch0, 0, 4, 1, 1, 40)[0]
+    obs, exp_p, bins = _binned_counts(samples, basis, p)
+    chi2 = ((obs - n_ch * exp_p) ** 2 / (n_ch * exp_p)).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-3
+    q = np.sqrt(p)
+    q /= q.sum()
+    exp_q = np.bincount(bins, weights=q, minlength=len(obs))
+    chi2_q = ((obs - n_ch * exp_q) ** 2 / (n_ch * exp_q)).sum()
+    assert stats.chi2.sf(chi2_q, len(obs) - 1) < 1e-6
+
+
 # ---------------------------------------------------------------- SR
 @pytest.fixture(scope='module')
 def small_sr():
