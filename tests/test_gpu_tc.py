@@ -128,6 +128,35 @@ def test_local_energy_bf16_zero_network():
     assert np.all(e[:, 0] == 75.0) and np.all(e[:, 1] == 0.0)
 
 
+def test_local_energy_bf16_largest_lattice(monkeypatch):
+    """36 x 36 (the largest lattice of the serving mix; 16 channels, 7
+    layers; the plain paths' per-block working sets do not fit on chip at
+    this size): a zero network gives exactly (J1 + J2) N / 2 for every
+    sample, log psi agrees with the oracle's forward, and the cone-restricted
+    local energy equals the dense one bitwise."""
+    from tests.gpu_common import problem_of
+    w = WL['j1j2_10x10']
+    over = {'L': 36, 'n_up': 648, 'n_down': 648, 'n_layers': 7}
+    P = lib().nqs_param_count(problem_of(w, **over))
+    cfg_h = configs_for(w, 6, seed=27, **over)
+    cfg = dev(cfg_h)
+    zero, _ = make_ctx(w, params=np.zeros(P), **over)
+    e0 = zero.local_energy(cfg, None, 'bf16').cpu().numpy()
+    assert np.all(e0[:, 0] == 0.75 * 1296) and np.all(e0[:, 1] == 0.0)
+    ctx, params = make_ctx(w, param_seed=28, **over)
+    spec, _ = oracle_of(w, **over)
+    a, phi = cnn.forward(params, cfg_h[:3], spec)
+    lp = ctx.logpsi(cfg[:3], 'bf16').cpu().numpy()
+    # the bf16 rounding of 1,296 sites' activations shifts log psi by a nearly common offset (about 4e-6 per
+    # site); ratios of amplitudes, which the sampler and E_loc use, cancel it
+    assert np.abs(lp[:, 0] - a).max() <= 1e-5 * 1296 and np.abs(lp[:, 1] - phi).max() <= 1e-5 * 1296
+    assert np.abs((lp[1:, 0] - lp[0, 0]) - (a[1:] - a[0])).max() <= 1e-3
+    e = ctx.local_energy(cfg, None, 'bf16')
+    assert bool(torch.isfinite(e).all())
+    monkeypatch.setenv('NQS_TC_DENSE', '1')
+    assert torch.equal(ctx.local_energy(cfg, None, 'bf16'), e)
+
+
 def test_bf16_unsupported_shapes_fail_loudly():
     nqs = lib()
     w = WL['j1j2_4x4']          # 4 channels: below the tensor-core N granularity
