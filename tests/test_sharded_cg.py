@@ -105,3 +105,40 @@ def test_two_rank_cg_equals_unsharded_cg():
     # and CG reaches the dense solve
     x_dense, _ = sr.solve_dense(dA, dPhi, eloc, 1e-3)
     assert np.abs(out[0][1] - x_dense).max() <= 1e-8 * np.abs(x_dense).max()
+
+
+def _dying_worker(rank, world, port, q):
+    """Rank 1 exits after the first collective (a dead rank); rank 0 must get
+    an error from its next collective instead of waiting for ever."""
+    import datetime
+    os.environ['MASTER_ADDR'] = '127.0.0.1'
+    os.environ['MASTER_PORT'] = str(port)
+    dist.init_process_group('gloo', rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    dA, dPhi, eloc = _inputs()
+    ns = dA.shape[0]
+    rows = np.array_split(np.arange(ns), world)[rank]
+    _allreduce(dA[rows].sum(0))
+    if rank == 1:
+        os._exit(0)
+    try:
+        sharded_cg(dA[rows], dPhi[rows], eloc[rows], ns, 1e-3, 1e-10, 500)
+        q.put((rank, 'finished'))
+    except Exception as e:    # the failure is reported, the process stays usable
+        q.put((rank, 'error:' + type(e).__name__))
+
+
+def test_dead_rank_is_reported_not_waited_for():
+    import time
+    ctx = mp.get_context('spawn')
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    rank, status = q.get(timeout=120)
+    assert rank == 0 and status.startswith('error:')
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert time.time() - t0 < 100
