@@ -59,7 +59,8 @@ typedef enum {
     NQS_ERR_NONFINITE = -4,
     NQS_ERR_NOT_CONVERGED = -5,
     NQS_ERR_TIMEOUT = -6,
-    NQS_ERR_UNSUPPORTED = -7
+    NQS_ERR_UNSUPPORTED = -7,
+    NQS_ERR_BOUNDS = -8
 } nqs_status;
 
 typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_BF16 = 2 } nqs_precision;
@@ -149,6 +150,17 @@ int nqs_set_sm_limit(nqs_ctx *ctx, int32_t sms);
  * NQS_ERR_TIMEOUT and clears it, and the context stays usable. No GPU fault
  * or hang is involved. iterations: 1 .. 1e6 (else NQS_ERR_INVALID_ARG). */
 int nqs_probe_wait_timeout(nqs_ctx *ctx, int64_t iterations);
+
+/* Device-side index checks. A library built with NQS_CHECK defined (see
+ * paper_2204_07816_gb300/build.py, checked=True) tests every data-dependent
+ * index of its kernels (sampled sites, connected pairs, table entries, row
+ * destinations) before the access; an index out of range skips the access
+ * and sets the bounds bit, which the next nqs_sync returns as
+ * NQS_ERR_BOUNDS (then clears). In the default build the checks compile
+ * away. nqs_probe_bounds enqueues a one-thread kernel that reports a failed
+ * check without any access, so the reporting path is tested in either build;
+ * the context stays usable. */
+int nqs_probe_bounds(nqs_ctx *ctx);
 
 /* Number of GPU kernels this context has launched so far (a monotone
  * counter for accounting; -1 if ctx is NULL). Host only. */

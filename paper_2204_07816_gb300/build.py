@@ -1,6 +1,11 @@
 """Build the CUDA library in-tree: every csrc/*.cu is compiled for sm_103a
 in parallel and linked into libnqs.so beside this file. A content hash of
-the sources and flags skips the rebuild when nothing changed."""
+the sources and flags skips the rebuild when nothing changed.
+
+build(checked=True) makes libnqs_checked.so instead, compiled with NQS_CHECK:
+every data-dependent index of the kernels is tested before use and a failure
+is reported by nqs_sync as NQS_ERR_BOUNDS (a device-side stand-in for a
+memory checker). Load it with NQS_LIBRARY=<path> before importing nqs."""
 
 import concurrent.futures
 import hashlib
@@ -14,6 +19,8 @@ CSRC = os.path.join(HERE, 'csrc')
 INCLUDE = os.path.join(ROOT, 'include')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(HERE, 'libnqs.so')
+BUILD_CHECKED = os.path.join(HERE, '_build_checked')
+LIB_CHECKED = os.path.join(HERE, 'libnqs_checked.so')
 
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-std=c++17', '-O3', '-lineinfo', '--expt-relaxed-constexpr', '-Xcompiler', '-fPIC',
@@ -29,7 +36,7 @@ def _sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith('.cu'))
 
 
-def _digest():
+def _digest(flags):
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)) + ['../../include/nqs.h']:
         path = os.path.normpath(os.path.join(CSRC, name))
@@ -37,23 +44,25 @@ def _digest():
             h.update(name.encode())
             with open(path, 'rb') as f:
                 h.update(f.read())
-    h.update(' '.join(ARCH + FLAGS).encode())
+    h.update(' '.join(ARCH + flags).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
 
-def build(verbose=False, force=False):
-    """Compile and link libnqs.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, 'stamp')
-    digest = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == digest:
-        return LIB
+def build(verbose=False, force=False, checked=False):
+    """Compile and link libnqs.so (libnqs_checked.so if checked); returns its path."""
+    bdir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    flags = FLAGS + (['-DNQS_CHECK=1'] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
+    stamp = os.path.join(bdir, 'stamp')
+    digest = _digest(flags)
+    if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == digest:
+        return lib
     nvcc = _nvcc()
 
     def compile_one(name):
-        obj = os.path.join(BUILD, name[:-3] + '.o')
-        cmd = [nvcc] + ARCH + FLAGS + ['-c', os.path.join(CSRC, name), '-o', obj]
+        obj = os.path.join(bdir, name[:-3] + '.o')
+        cmd = [nvcc] + ARCH + flags + ['-c', os.path.join(CSRC, name), '-o', obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError('nvcc failed for %s:\n%s\n%s' % (name, ' '.join(cmd), r.stderr))
@@ -63,16 +72,16 @@ def build(verbose=False, force=False):
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + '.tmp'
+    tmp = lib + '.tmp'
     cmd = [nvcc] + ARCH + ['-shared', '-cudart', 'static', '-o', tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError('link failed:\n%s\n%s' % (' '.join(cmd), r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, 'w') as f:
         f.write(digest)
-    return LIB
+    return lib
 
 
 if __name__ == '__main__':
-    print(build(verbose='-v' in sys.argv, force='-f' in sys.argv))
+    print(build(verbose='-v' in sys.argv, force='-f' in sys.argv, checked='--checked' in sys.argv))

@@ -223,7 +223,7 @@ int nqs_sync(nqs_ctx *c) {
         cudaMemset(c->err_dev, 0, sizeof(int));
         if (bits & ERRBIT_NONFINITE) return fail(c, NQS_ERR_NONFINITE, "a kernel produced a non-finite value");
         if (bits & ERRBIT_TIMEOUT) return fail(c, NQS_ERR_TIMEOUT, "a device-side wait ran out of iterations");
-        return fail(c, NQS_ERR_CUDA, "a device-side bounds check failed");
+        return fail(c, NQS_ERR_BOUNDS, "a device-side index check failed");
     }
     return NQS_OK;
 }
@@ -256,6 +256,12 @@ int nqs_probe_wait_timeout(nqs_ctx *c, int64_t iterations) {
     if (iterations < 1 || iterations > 1000000) return fail(c, NQS_ERR_INVALID_ARG, "nqs_probe_wait_timeout: bad count");
     LaunchEnv env = env_of(c);
     return launch_wait_probe(iterations, env);
+}
+
+int nqs_probe_bounds(nqs_ctx *c) {
+    if (int rc = check_ctx(c)) return rc;
+    LaunchEnv env = env_of(c);
+    return launch_bounds_probe(env);
 }
 
 int nqs_destroy(nqs_ctx *c) {

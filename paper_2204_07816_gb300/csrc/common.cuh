@@ -13,6 +13,14 @@ namespace nqs {
 // Device-side error bits latched in the context (read by nqs_sync).
 enum : int { ERRBIT_NONFINITE = 1, ERRBIT_TIMEOUT = 2, ERRBIT_BOUNDS = 4 };
 
+// Index check of the checked build (NQS_CHECK): false, with the bounds bit set, when cond fails; the caller then
+// skips the access. In the default build it is the constant true and compiles away.
+#ifdef NQS_CHECK
+#define NQS_INDEX_OK(cond, err) ((cond) ? true : (atomicOr((err), ERRBIT_BOUNDS), false))
+#else
+#define NQS_INDEX_OK(cond, err) true
+#endif
+
 struct Problem {
     int model;      // NQS_MODEL_J1J2 / NQS_MODEL_TJ
     int L, N;

@@ -97,6 +97,7 @@ struct TcMultiItem {
 size_t tc_multi_table_bytes(int count);
 int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, int max_blocks, const LaunchEnv &env);
 int launch_wait_probe(int64_t iterations, const LaunchEnv &env);
+int launch_bounds_probe(const LaunchEnv &env);
 // Tensor-core plan the launchers choose (host only): kind 0 log psi, 1 local
 // energy, 2 sampler (n = chains). out[8]: G, slots, blocks per SM, epilogue
 // warps, tiles per group, shared bytes per block, TMEM columns, grid.

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kThreads) eloc_plain_kernel(Problem p, const T
                 int v = sigma[site];
                 if (k >= 0) {
                     const int i = ci[k], j = cj[k];
-                    if (site == i) v = sigma[j];
+                    if (!NQS_INDEX_OK(k < nconn && i >= 0 && i < N && j >= 0 && j < N, err)) v = 0;
+                    else if (site == i) v = sigma[j];
                     else if (site == j) v = sigma[i];
                 }
                 spins[r] = (int8_t)v;
@@ -263,7 +264,9 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
             if (threadIdx.x == 0) {
                 int cnt = 0;
                 for (int g = 0; g < gc; ++g)
-                    if (cur[g * N + pi[g]] != cur[g * N + pj[g]]) list[cnt++] = g;
+                    if (NQS_INDEX_OK(pi[g] >= 0 && pi[g] < N && pj[g] >= 0 && pj[g] < N, err) &&
+                        cur[g * N + pi[g]] != cur[g * N + pj[g]])
+                        list[cnt++] = g;
                 list[G] = cnt;
                 scnt[0] += (unsigned long long)cnt;
             }
@@ -594,6 +597,19 @@ int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const 
         grad_plain_kernel<float><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, O,
                                                                        (float *)scratch, grad_per_block(p));
     return check_launch(env, "grad_plain_kernel");
+}
+
+// Reports one failed index check without touching memory (the host-side reporting path of the checked build).
+__global__ void bounds_probe_kernel(int *err) {
+    if (!NQS_INDEX_OK(false, err)) return;
+    atomicOr(err, ERRBIT_BOUNDS);   // the default build's check is a constant true: report the failure directly
+}
+
+int launch_bounds_probe(const LaunchEnv &env) {
+    bounds_probe_kernel<<<1, 1, 0, env.stream>>>(env.err);
+    if (cudaGetLastError() != cudaSuccess) { *env.msg = "bounds probe launch failed"; return NQS_ERR_CUDA; }
+    ++*env.launches;
+    return NQS_OK;
 }
 
 }  // namespace nqs

@@ -411,6 +411,11 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
                 const float h1 = C == 16 ? hb[(2 * c + 1) % HB] : 0.5f * bias[2 * c + 1];
                 w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
             }
+            if (!NQS_INDEX_OK(((dst.x & 0xFFFFu) == kNone || (dst.x & 0xFFFFu) < (uint32_t)pl.rbuf) &&
+                                  ((dst.x >> 16) == kNone || (dst.x >> 16) < (uint32_t)pl.rbuf) &&
+                                  ((dst.y & 0xFFFFu) == kNone || (dst.y & 0xFFFFu) < (uint32_t)pl.rbuf) &&
+                                  ((dst.y >> 16) == kNone || (dst.y >> 16) < (uint32_t)pl.rbuf), err))
+                continue;
             store_rows<C>(pl, out, dst, w);
             if (cache_w) {   // the sample itself (configuration 0) fills the cache
                 const uint32_t pos = main / (uint32_t)pl.G;
@@ -740,7 +745,8 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
                     int s0 = site + roll[c] * L;   // original site: row + roll (mod L)
                     if (s0 >= N) s0 -= N;
                     const int i = ci[k], j = cj[k];
-                    v = sigma[s0 == i ? j : (s0 == j ? i : s0)];
+                    v = NQS_INDEX_OK(k >= 0 && k < nconn && i >= 0 && i < N && j >= 0 && j < N && s0 >= 0, err)
+                            ? sigma[s0 == i ? j : (s0 == j ? i : s0)] : 0;
                 }
                 sh.spins[r] = (int8_t)v;
             }
@@ -934,7 +940,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
                 int cnt = 0;
                 for (int g = 0; g < G; ++g) {
                     const int c = s * G + g;
-                    if (c < gc && cur[c * N + pi_s[c]] != cur[c * N + pj_s[c]]) list[s * (G + 1) + cnt++] = c;
+                    if (c < gc && NQS_INDEX_OK(pi_s[c] >= 0 && pi_s[c] < N && pj_s[c] >= 0 && pj_s[c] < N, err) &&
+                        cur[c * N + pi_s[c]] != cur[c * N + pj_s[c]])
+                        list[s * (G + 1) + cnt++] = c;
                 }
                 list[s * (G + 1) + G] = cnt;
             }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, 'libnqs.so')
 
 NQS_OK = 0
 STATUS = {0: 'NQS_OK', -1: 'NQS_ERR_INVALID_ARG', -2: 'NQS_ERR_OOM', -3: 'NQS_ERR_CUDA', -4: 'NQS_ERR_NONFINITE',
-          -5: 'NQS_ERR_NOT_CONVERGED', -6: 'NQS_ERR_TIMEOUT', -7: 'NQS_ERR_UNSUPPORTED'}
+          -5: 'NQS_ERR_NOT_CONVERGED', -6: 'NQS_ERR_TIMEOUT', -7: 'NQS_ERR_UNSUPPORTED', -8: 'NQS_ERR_BOUNDS'}
 NQS_ERR_NOT_CONVERGED = -5
 NQS_ERR_UNSUPPORTED = -7
 PRECISION = {'fp64': 0, 'fp32': 1, 'bf16': 2}
@@ -27,7 +27,8 @@ EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
            'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve',
-           'nqs_sr_solve_woodbury', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_set_sm_limit', 'nqs_sampler_counts')
+           'nqs_sr_solve_woodbury', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_probe_bounds', 'nqs_set_sm_limit',
+           'nqs_sampler_counts')
 
 
 class nqs_problem(ctypes.Structure):
@@ -46,11 +47,14 @@ class NQSError(RuntimeError):
 _lib = None
 
 
-def load(path=LIB_PATH):
-    """Load libnqs.so (raises OSError if it has not been built)."""
+def load(path=None):
+    """Load libnqs.so (raises OSError if it has not been built). path
+    defaults to $NQS_LIBRARY (another build, for instance the checked
+    libnqs_checked.so), else the in-tree libnqs.so."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get('NQS_LIBRARY') or LIB_PATH
     if not os.path.exists(path):
         raise OSError('libnqs.so not found at %s: run paper_2204_07816_gb300/build.py' % path)
     lib = ctypes.CDLL(path)
@@ -64,6 +68,7 @@ def load(path=LIB_PATH):
         'nqs_sync': (ctypes.c_int, [P]),
         'nqs_kernel_launches': (I64, [P]),
         'nqs_probe_wait_timeout': (ctypes.c_int, [P, I64]),
+        'nqs_probe_bounds': (ctypes.c_int, [P]),
         'nqs_set_sm_limit': (ctypes.c_int, [P, I32]),
         'nqs_sampler_counts': (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), I32]),
         'nqs_logpsi': (ctypes.c_int, [P, P, I64, P, I32]),
@@ -290,6 +295,11 @@ class Context:
         """nqs_probe_wait_timeout: a bounded device wait that runs out; the
         next sync() raises NQSError with NQS_ERR_TIMEOUT."""
         self._check(self.lib.nqs_probe_wait_timeout(self.ctx, int(iterations)))
+
+    def probe_bounds(self):
+        """nqs_probe_bounds: report one failed device-side index check; the
+        next sync() raises NQSError with NQS_ERR_BOUNDS."""
+        self._check(self.lib.nqs_probe_bounds(self.ctx))
 
     def get_chains(self, n_chains):
         out = torch.empty((n_chains, self.N), dtype=torch.int8, device=self.device)

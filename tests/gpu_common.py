@@ -12,8 +12,14 @@ WL = nqs_synth.WORKLOADS
 
 
 def lib():
-    from paper_2204_07816_gb300 import build, nqs
-    build.build()
+    """Build and load the library; with NQS_CHECKED=1 the checked build (device-side index checks)."""
+    import os
+    from paper_2204_07816_gb300 import build
+    if os.environ.get('NQS_CHECKED') == '1':
+        os.environ['NQS_LIBRARY'] = build.build(checked=True)
+    else:
+        build.build()
+    from paper_2204_07816_gb300 import nqs
     return nqs
 
 

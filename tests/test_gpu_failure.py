@@ -38,3 +38,19 @@ def test_probe_rejects_bad_counts():
         with pytest.raises(nqs.NQSError):
             ctx.probe_wait_timeout(bad)
     ctx.sync()
+
+
+def test_bounds_probe_is_reported_and_cleared():
+    """The reporting path of the device-side index checks: a failed check
+    makes the next sync raise NQS_ERR_BOUNDS, and the context stays usable."""
+    nqs = lib()
+    w = WL['j1j2_4x4']
+    ctx, _ = make_ctx(w)
+    cfg = dev(configs_for(w, 4, seed=3))
+    before = ctx.local_energy(cfg, None, 'fp64').clone()
+    ctx.probe_bounds()
+    with pytest.raises(nqs.NQSError) as ei:
+        ctx.sync()
+    assert ei.value.code == -8
+    ctx.sync()
+    assert torch.equal(ctx.local_energy(cfg, None, 'fp64'), before)
