@@ -43,6 +43,7 @@ struct nqs_ctx {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int64_t launches = 0;
+    int cg_hint = 0;               // iterations of the last CG solve (sizes the next solve's first launch batch)
     void *multi_table = nullptr;   // request table of grouped launches led by this context
     size_t multi_table_bytes = 0;
     std::string msg;
@@ -493,10 +494,11 @@ int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, dou
     // limit, so the solve's rounding does not depend on the share a context
     // holds (its kernels are short; they do not pin SMs)
     env.num_sms = c->num_sms;
-    int iters = 0;
+    int iters = c->cg_hint;
     double resid = 0.0, energy[2] = {0.0, 0.0};
     const int rc = run_sr_solve(c->p, O, eloc, n, eps, rtol, max_iter, lr, delta, c->params, apply_update,
                                 (double *)c->scratch, &iters, &resid, energy, env);
+    if (rc == NQS_OK || rc == NQS_ERR_NOT_CONVERGED) c->cg_hint = iters;
     if (iters_out) *iters_out = iters;
     if (resid_out) *resid_out = resid;
     if (energy_out) { energy_out[0] = energy[0]; energy_out[1] = energy[1]; }

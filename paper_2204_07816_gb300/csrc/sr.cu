@@ -539,7 +539,10 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
 
     double host_sc[S_COUNT];
     int done_iters = 0;
-    int batch = 4;
+    // iterations launched between host checks: the caller's hint (*iters_out on entry: the previous solve's
+    // count) plus two, so a solve like the last one needs one check; then doubling. Launches past convergence
+    // return at once (device flag), so the hint changes no result.
+    int batch = iters_out && *iters_out > 0 ? std::min(std::max(*iters_out + 2, 4), 64) : 4;
     while (max_iter > 0) {
         for (int b = 0; b < batch; ++b) {
             gemv_rows_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(O, p, rows, P, y, sc);
