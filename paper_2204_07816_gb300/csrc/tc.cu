@@ -18,10 +18,13 @@
 // interior output also to its periodic images (a per-row destination table
 // built once per kernel). Each 128-row tile commits to its own mbarrier, so
 // the epilogue of tile t overlaps the MMAs of later tiles; two dedicated
-// warps issue the MMAs while eight warps run epilogues. Two groups ("slots") are in
-// flight: while the CUDA cores run the epilogue of one slot's layer, the
-// tensor core runs the other slot's MMAs. The next layer's weights stream
-// in by bulk copy (TMA) into a double buffer while the current layer runs.
+// warps issue the MMAs while four or eight warps run epilogues. A plan keeps
+// one or two groups ("slots") in flight per block, and one or two blocks per
+// SM: while the CUDA cores run the epilogue of one group's layer, the tensor
+// core runs another group's MMAs. The next layer's weights stream in by
+// bulk copy (cp.async.bulk) into a double buffer while the current layer
+// runs. One-block plans evaluate each connected configuration of a local
+// energy on its cone only (struct Band below).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
