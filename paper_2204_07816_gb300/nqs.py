@@ -194,14 +194,15 @@ class Context:
             raise NQSError(-1, 'invalid problem')
         if params.numel() != self.P:
             raise ValueError('params has %d entries, problem needs %d' % (params.numel(), self.P))
+        pptr = _ptr(params, torch.float64, 'params')   # a float64 CUDA tensor, checked before any CUDA call
         self.device = params.device
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         self.ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            rc = lib.nqs_init(ctypes.byref(self.ctx), ctypes.byref(problem), _ptr(params, torch.float64, 'params'),
-                              ctypes.c_uint64(seed), ctypes.c_void_p(stream.cuda_stream))
+            rc = lib.nqs_init(ctypes.byref(self.ctx), ctypes.byref(problem), pptr, ctypes.c_uint64(seed),
+                              ctypes.c_void_p(stream.cuda_stream))
         if rc != NQS_OK:
             raise NQSError(rc, lib.nqs_last_error(None).decode())
 

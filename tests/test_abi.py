@@ -66,3 +66,24 @@ def test_invalid_problems_rejected(nqs, bad):
 
 def test_null_problem_rejected(nqs):
     assert nqs.load().nqs_param_count(None) == -1
+
+
+def test_binding_rejects_host_and_misshaped_tensors(nqs):
+    """Argument marshalling fails before any device work: parameters must be
+    a float64 CUDA tensor of the problem's length (checked on the host)."""
+    import torch
+    prob = nqs.make_problem('j1j2', 4, n_layers=2, channels=4)
+    P = nqs.nqs_param_count(prob)
+    with pytest.raises(ValueError):
+        nqs.Context(prob, torch.zeros(P + 1, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        nqs.Context(prob, torch.zeros(P, dtype=torch.float64))          # a host tensor
+    with pytest.raises(TypeError):
+        nqs._ptr(torch.zeros(3, dtype=torch.float32), torch.float64, 'x')
+
+
+def test_status_names_cover_the_header(nqs):
+    """Every status code the header declares has a name in the binding."""
+    header = open(os.path.join(ROOT, 'include', 'nqs.h')).read()
+    codes = {int(v) for v in re.findall(r'NQS_(?:OK|ERR_[A-Z_]+) = (-?\d+)', header)}
+    assert codes <= set(nqs.STATUS)
