@@ -30,8 +30,8 @@
  *   the work is enqueued; the outputs are valid after the stream has
  *   reached that point (nqs_sync waits for it). Argument errors are
  *   returned at once. Errors that the GPU finds (a non-finite value, a wait
- *   that ran out of iterations) are latched in the context and returned by
- *   the next nqs_sync.
+ *   that ran out of iterations, a failed index check of the checked build)
+ *   are latched in the context and returned by the next nqs_sync.
  * - Return values: NQS_OK or a negative nqs_status. On error the outputs
  *   are unspecified and the chain state is unchanged. nqs_last_error gives
  *   a one-line description.
@@ -114,7 +114,7 @@ int nqs_tc_plan(const nqs_problem *p, int32_t kind, int64_t n, int32_t max_smem_
  * sm_100-family device is current. */
 int nqs_init(nqs_ctx **out, const nqs_problem *p, double *params, uint64_t seed, void *stream);
 
-/* Wait for the context's stream and frees every resource. Returns the
+/* Waits for the context's stream and frees every resource. Returns the
  * latched device error, if any. */
 int nqs_destroy(nqs_ctx *ctx);
 
@@ -290,8 +290,9 @@ int nqs_sr_solve(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, d
  *   delta = Ohat^T y,
  * equal to the solution of (S + eps I) delta = F because
  * (Ohat^T Ohat / n + eps I)^-1 Ohat^T = Ohat^T (Ohat Ohat^T / n + eps I)^-1.
- * Work: (2n)^2 P + (2n)^3 / 3 multiply-adds, against 4 n P per CG
- * iteration, so it pays when CG needs more than about n / 2 iterations.
+ * Work: 2 n^2 P (Gram matrix, lower half) + (2n)^3 / 6 (Cholesky)
+ * multiply-adds, against 4 n P per CG iteration, so it pays when CG needs
+ * more than about n / 2 iterations.
  * Arguments as nqs_sr_solve; eps must be > 0 and n <= 32,768 (workspace
  * (2n)^2 float64, owned by the context). refine_steps (0..8): steps of
  * iterative refinement, each recomputing the sample-space residual
