@@ -429,12 +429,22 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
                 }
             }
         } else {
+            // biases and head weights as 16-byte broadcast loads (the fp32 block is 16-byte aligned and every
+            // offset a multiple of 16 floats); the sums run over c = 0 .. C - 1 in order as before
             float ca = 0.f, cp = 0.f;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float hv = ptx::silu_fast(v[c] + bias[c]);
-                ca = fmaf(wa[c], hv, ca);
-                cp = fmaf(wa[C + c], hv, cp);
+            for (int c4 = 0; c4 < C; c4 += 4) {
+                const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
+                const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
+                const float4 xp = *reinterpret_cast<const float4 *>(wa + C + c4);
+                const float bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {xa.x, xa.y, xa.z, xa.w};
+                const float pp[4] = {xp.x, xp.y, xp.z, xp.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float hv = ptx::silu_fast(v[c4 + k] + bb[k]);
+                    ca = fmaf(aa[k], hv, ca);
+                    cp = fmaf(pp[k], hv, cp);
+                }
             }
             // configuration-major ([a | phi][g][padded position p], row = p * G + g), so that the head's
             // reads of one configuration's sites are consecutive words
