@@ -130,3 +130,100 @@ def tj_bruteforce(basis, L, t, J):
         vals.append(diag)
     M = len(states)
     return sp.csr_matrix((vals, (rows, cols)), shape=(M, M))
+
+
+def _apply_ops_vec(states, ops):
+    """Operators ('c'|'a', mode) applied right to left to an array of
+    occupation bit strings (uint64). Each operator on mode m carries the sign
+    (-1)^(number of occupied modes below m). Returns the new strings, their
+    signs and a mask of the strings the product does not annihilate."""
+    one = np.uint64(1)
+    st = states.copy()
+    sign = np.ones(len(st), dtype=np.int64)
+    alive = np.ones(len(st), dtype=bool)
+    for kind, m in reversed(ops):
+        bit = one << np.uint64(m)
+        occ = (st & bit) != 0
+        alive &= ~occ if kind == 'c' else occ
+        sign = np.where(np.bitwise_count(st & (bit - one)) & 1, -sign, sign)
+        st = (st | bit) if kind == 'c' else (st & ~bit)
+    return st, sign, alive
+
+
+def tj_bruteforce_vec(basis, L, t, J):
+    """The same second-quantised construction as tj_bruteforce (mode of
+    (site, spin) = spin * N + site), evaluated for all basis states at once
+    with array bit operations; used where the per-state loop is too slow."""
+    N = L * L
+    b = np.asarray(basis)
+    w = np.uint64(1) << np.arange(N, dtype=np.uint64)
+    states = ((b == 1).astype(np.uint64) * w).sum(1, dtype=np.uint64) | \
+        (((b == -1).astype(np.uint64) * w).sum(1, dtype=np.uint64) << np.uint64(N))
+    order = np.argsort(states)
+    sorted_states = states[order]
+    low = (np.uint64(1) << np.uint64(N)) - np.uint64(1)
+    M = len(states)
+    src = np.arange(M)
+    nn, _ = lattice_pairs(L, nnn=False)
+    rows, cols, vals = [src], [src], []
+    diag = np.zeros(M)
+
+    def bit(m):
+        return ((states >> np.uint64(m)) & np.uint64(1)).astype(np.int64)
+
+    def add(ops, coef):
+        st, sg, alive = _apply_ops_vec(states, ops)
+        alive &= ((st & (st >> np.uint64(N))) & low) == 0     # no doubly occupied site
+        st, sg, k = st[alive], sg[alive], src[alive]
+        pos = np.searchsorted(sorted_states, st)
+        assert np.all(sorted_states[pos] == st)
+        rows.append(order[pos])
+        cols.append(k)
+        vals.append(coef * sg)
+
+    for i, j in nn:
+        for spin in (0, 1):
+            for a, c in ((i, j), (j, i)):
+                add([('c', spin * N + a), ('a', spin * N + c)], -t)
+        nu_i, nd_i, nu_j, nd_j = bit(i), bit(N + i), bit(j), bit(N + j)
+        diag += J * ((nu_i - nd_i) * (nu_j - nd_j) / 4.0 - (nu_i + nd_i) * (nu_j + nd_j) / 4.0)
+        add([('c', i), ('a', N + i), ('c', N + j), ('a', j)], 0.5 * J)
+        add([('c', N + i), ('a', i), ('c', j), ('a', N + j)], 0.5 * J)
+    vals.insert(0, diag)
+    H = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(M, M))
+    H.sum_duplicates()
+    return H
+
+
+def gauge_equivalent(A, B):
+    """True iff A = D B D for a diagonal D of +-1 (A, B real sparse, same
+    shape). D is propagated along a breadth-first tree of A's off-diagonal
+    graph, then the identity is checked on every entry (exact for dyadic
+    values)."""
+    from scipy.sparse import csgraph
+    A = sp.csr_matrix(A)
+    B = sp.csr_matrix(B)
+    if A.shape != B.shape or not np.array_equal(A.diagonal(), B.diagonal()):
+        return False
+    Ad = (A - sp.diags(A.diagonal())).tocsr()
+    Bd = (B - sp.diags(B.diagonal())).tocsr()
+    Ad.eliminate_zeros()
+    Bd.eliminate_zeros()
+    if (abs(Ad) != abs(Bd)).nnz:
+        return False
+    R = Ad.sign().multiply(Bd.sign()).tocsr()      # A_rc / B_rc on the common pattern
+    M = A.shape[0]
+    d = np.zeros(M)
+    n_comp, labels = csgraph.connected_components(Ad, directed=False)
+    for comp in range(n_comp):
+        root = int(np.flatnonzero(labels == comp)[0])
+        seq, pred = csgraph.breadth_first_order(Ad, root, directed=False, return_predecessors=True)
+        d[root] = 1.0
+        child = seq[1:]
+        ratio = np.asarray(R[pred[child], child]).ravel()
+        for c, p, r in zip(child.tolist(), pred[child].tolist(), ratio.tolist()):
+            d[c] = r * d[p]
+    D = sp.diags(d)
+    diff = (D @ Bd @ D - Ad).tocsr()
+    diff.eliminate_zeros()
+    return diff.nnz == 0

@@ -100,6 +100,47 @@ def test_backward_matches_central_differences(L, c_in, C, n_l, nu, nd):
     assert np.allclose(dA[:, P - 2 * C:P - C], dPhi[:, P - C:], rtol=0, atol=0)
 
 
+def _blocks(c_in, C, n_l):
+    """(offset, size) of every parameter block in the flat layout: per conv
+    layer W[C_out][C_in][3][3] then b[C_out], then the head w_a[C], w_phi[C]."""
+    out, off = [], 0
+    for layer in range(n_l):
+        cin = c_in if layer == 0 else C
+        out += [(off, 9 * cin * C), (off + 9 * cin * C, C)]
+        off += 9 * cin * C + C
+    return out + [(off, C), (off + C, C)]
+
+
+@pytest.mark.parametrize('L,c_in,C,n_l,nu,nd', [(10, 1, 16, 6, 50, 50), (12, 3, 32, 6, 63, 63)])
+def test_backward_matches_central_differences_at_full_size(L, c_in, C, n_l, nu, nd):
+    """The 10x10 J1-J2 and 12x12 t-J networks: a seeded random subset of
+    parameters, at least eight from every weight, bias and head block,
+    h = 1e-5, relative 1e-6."""
+    spec = _spec(L, c_in, C, n_l)
+    params = nqs_synth.random_params(c_in, C, n_l, seed=15)
+    cfg = nqs_synth.random_configs(L * L, nu, nd, 2, seed=16)
+    _, _, dA, dPhi = cnn.backward(params, cfg, spec)
+    blocks = _blocks(c_in, C, n_l)
+    assert blocks[-1][0] + blocks[-1][1] == params.size
+    rng = np.random.default_rng(17)
+    ks = np.concatenate([off + rng.choice(size, min(size, 8), replace=False) for off, size in blocks])
+    h = 1e-5
+    fa = np.zeros((2, ks.size))
+    fp = np.zeros((2, ks.size))
+    for n, k in enumerate(ks):
+        pp = params.copy()
+        pm = params.copy()
+        pp[k] += h
+        pm[k] -= h
+        ap, php = cnn.forward(pp, cfg, spec)
+        am, phm = cnn.forward(pm, cfg, spec)
+        fa[:, n] = (ap - am) / (2 * h)
+        fp[:, n] = (php - phm) / (2 * h)
+    scale = max(np.abs(fa).max(), np.abs(fp).max())
+    assert np.abs(dA[:, ks] - fa).max() <= 1e-6 * scale
+    assert np.abs(dPhi[:, ks] - fp).max() <= 1e-6 * scale
+
+
 @pytest.fixture(scope='module')
 def enum_4x4():
     spec = _spec(4, 1, 4, 2)

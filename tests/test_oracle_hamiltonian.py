@@ -103,41 +103,6 @@ def test_connected_configs_conserve_particle_numbers():
             assert s[i] != s[j]
 
 
-def _gauge_equivalent(A, B):
-    """True iff A = D B D for a diagonal D of +-1 (A, B sparse, same shape)."""
-    A = A.tocsr()
-    B = B.tocsr()
-    if not np.array_equal(A.diagonal(), B.diagonal()):
-        return False
-    Ad = (A - sp.diags(A.diagonal())).tocsr()
-    Bd = (B - sp.diags(B.diagonal())).tocsr()
-    Ad.eliminate_zeros()
-    Bd.eliminate_zeros()
-    if (abs(Ad) != abs(Bd)).nnz:
-        return False
-    M = A.shape[0]
-    d = np.zeros(M)
-    Ac, Bc = Ad.tocoo(), Bd.tocsr()
-    adj = [[] for _ in range(M)]
-    for r, c, v in zip(Ac.row, Ac.col, Ac.data):
-        adj[r].append((c, v / Bc[r, c]))
-    for root in range(M):
-        if d[root]:
-            continue
-        d[root] = 1.0
-        stack = [root]
-        while stack:
-            r = stack.pop()
-            for c, ratio in adj[r]:
-                want = ratio * d[r]
-                if d[c] == 0:
-                    d[c] = want
-                    stack.append(c)
-                elif d[c] != want:
-                    return False
-    return True
-
-
 @pytest.mark.parametrize('L,nu,nd', [(3, 2, 2), (3, 3, 3), (4, 2, 1), (4, 2, 2)])
 def test_tj_fermion_signs_match_second_quantisation(L, nu, nd):
     """Snake-order hop signs equal brute-force fermion operator algebra under
@@ -145,19 +110,75 @@ def test_tj_fermion_signs_match_second_quantisation(L, nu, nd):
     basis = ed.sector_basis(L * L, nu, nd)
     Hs = ed.sparse_h(basis, hamiltonian.TJ(L, 1.0, 0.4))
     Hb = oracle_refs.tj_bruteforce(basis, L, 1.0, 0.4)
-    assert _gauge_equivalent(Hb, Hs)
+    assert oracle_refs.gauge_equivalent(Hb, Hs)
 
 
-def test_tj_sign_mistake_is_caught():
-    """The gauge check is sensitive: dropping the string sign breaks it."""
-    class NoSign(hamiltonian.TJ):
-        def connected_dense(self, configs):
-            d, H = super().connected_dense(configs)
-            return d, np.where(np.abs(H) == self.t, -self.t, H)
-    basis = ed.sector_basis(9, 3, 3)
-    Hs = ed.sparse_h(basis, NoSign(3, 1.0, 0.4))
-    Hb = oracle_refs.tj_bruteforce(basis, 3, 1.0, 0.4)
-    assert not _gauge_equivalent(Hb, Hs)
+class _NoString(hamiltonian.TJ):
+    """Planted mistake: hops without the fermion string sign."""
+    def connected_dense(self, configs):
+        d, H = super().connected_dense(configs)
+        return d, np.where(np.abs(H) == self.t, -self.t, H)
+
+
+class _SameSpinString(hamiltonian.TJ):
+    """Planted mistake: the string counts only electrons of the hopping
+    electron's spin (a spin-major ordering) while exchange stays unsigned."""
+    def connected_dense(self, configs):
+        d, H = super().connected_dense(configs)
+        c = np.asarray(configs, dtype=np.int64)
+        for k, (i, j, _) in enumerate(self.bonds):
+            hop = (c[:, i] == 0) != (c[:, j] == 0)
+            spin = c[:, i] + c[:, j]
+            lo, hi = sorted((self.snake[i], self.snake[j]))
+            mid = [q for q in range(c.shape[1]) if lo < self.snake[q] < hi]
+            n = (c[:, mid] == spin[:, None]).sum(1)
+            H[hop, k] = -self.t * (1.0 - 2.0 * (n[hop] % 2))
+        return d, H
+
+
+class _InclusiveString(hamiltonian.TJ):
+    """Planted mistake: the string also counts the far end of the bond."""
+    def connected_dense(self, configs):
+        d, H = super().connected_dense(configs)
+        c = np.asarray(configs, dtype=np.int64)
+        for k, (i, j, _) in enumerate(self.bonds):
+            hop = (c[:, i] == 0) != (c[:, j] == 0)
+            lo, hi = sorted((self.snake[i], self.snake[j]))
+            mid = [q for q in range(c.shape[1]) if lo < self.snake[q] <= hi]
+            n = (c[:, mid] != 0).sum(1)
+            H[hop, k] = -self.t * (1.0 - 2.0 * (n[hop] % 2))
+        return d, H
+
+
+@pytest.mark.parametrize('mistake', [_NoString, _SameSpinString, _InclusiveString])
+@pytest.mark.parametrize('L,nu,nd', [(3, 3, 3), (4, 2, 2)])
+def test_tj_sign_mistake_is_caught(mistake, L, nu, nd):
+    """The gauge check is sensitive: each planted string-sign mistake breaks it."""
+    basis = ed.sector_basis(L * L, nu, nd)
+    Hs = ed.sparse_h(basis, mistake(L, 1.0, 0.4))
+    Hb = oracle_refs.tj_bruteforce_vec(basis, L, 1.0, 0.4)
+    assert not oracle_refs.gauge_equivalent(Hb, Hs)
+
+
+@pytest.mark.parametrize('L,nu,nd', [(3, 3, 3), (4, 2, 1), (4, 2, 2)])
+def test_vectorised_bruteforce_equals_per_state_form(L, nu, nd):
+    """The array form of the operator algebra builds exactly the matrix of
+    the per-state loop."""
+    basis = ed.sector_basis(L * L, nu, nd)
+    Hb = oracle_refs.tj_bruteforce(basis, L, 1.0, 0.4)
+    Hv = oracle_refs.tj_bruteforce_vec(basis, L, 1.0, 0.4)
+    assert (Hb != Hv).nnz == 0
+
+
+def test_tj_fermion_signs_4x4_two_holes():
+    """4x4 with 2 holes and 7 + 7 electrons (411,840 states): snake-order
+    signs against the operator algebra, integer exact up to a +-1 gauge."""
+    basis = ed.sector_basis(16, 7, 7)
+    assert basis.shape == (411840, 16)
+    Hs = ed.sparse_h(basis, hamiltonian.TJ(4, 1.0, 0.4))
+    assert (Hs != Hs.T).nnz == 0
+    Hb = oracle_refs.tj_bruteforce_vec(basis, 4, 1.0, 0.4)
+    assert oracle_refs.gauge_equivalent(Hb, Hs)
 
 
 def test_tj_zero_doping_is_shifted_heisenberg(basis_4x4_sz0):
