@@ -87,3 +87,14 @@ def test_status_names_cover_the_header(nqs):
     header = open(os.path.join(ROOT, 'include', 'nqs.h')).read()
     codes = {int(v) for v in re.findall(r'NQS_(?:OK|ERR_[A-Z_]+) = (-?\d+)', header)}
     assert codes <= set(nqs.STATUS)
+
+
+def test_checked_build_exports_the_same_entry_points(nqs):
+    """The checked variant (device-side index checks, NQS_ERR_BOUNDS) builds
+    from the same sources and exports every declared entry point."""
+    from paper_2204_07816_gb300 import build
+    path = build.build(checked=True)
+    assert os.path.basename(path) != os.path.basename(nqs.LIB_PATH)
+    lib = ctypes.CDLL(path)
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
