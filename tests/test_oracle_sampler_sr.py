@@ -134,6 +134,20 @@ def test_sampler_chi_square_against_enumeration(exact_4x4, seed):
     assert stats.chi2.sf(chi2_q, len(obs) - 1) < 1e-6
 
 
+def test_sampler_mixes_from_a_common_start(exact_4x4):
+    """All 4,096 chains start from one striped state (rows alternately all up
+    and all down), so the chi-square against |psi|^2 after burn-in also tests
+    that the exchange moves connect the whole sector: a sampler that never
+    moves spins between rows keeps every row's magnetisation and fails."""
+    spec, params, basis, p = exact_4x4
+    stripes = np.repeat(np.array([1, -1, 1, -1], dtype=np.int8), 4)
+    n_ch = 4096
+    samples = sampler.metropolis(params, spec, np.tile(stripes, (n_ch, 1)), 0, 4, 1, 1, 29)[0]
+    obs, exp_p, _ = _binned_counts(samples, basis, p)
+    chi2 = ((obs - n_ch * exp_p) ** 2 / (n_ch * exp_p)).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-3
+
+
 def test_sampler_chi_square_tj_sector():
     """t-J 4x4 with 2 up, 2 down and 12 holes (10,920 states): hops and
     exchanges sample the enumerated |psi|^2, and the same counts reject
