@@ -38,6 +38,25 @@ def test_exchange_without_half(monkeypatch):
     _fails(ham_pins.test_j1j2_matrix_equals_kronecker_construction, basis, 0.0)
 
 
+def test_sign_rule_on_every_bond(monkeypatch):
+    """The sign rule flipping next-nearest-neighbour exchanges too (they keep
+    the up count of each sublattice, so the gauge leaves them alone): the
+    full-enumeration identity against the gauge-transformed Kronecker
+    Hamiltonian fails."""
+    setup = (cnn.NetSpec(4, 1, 4, 2), nqs_synth.random_params(1, 4, 2, seed=7, scale=1.5),
+             ed.sector_basis(16, 8, 8))
+    dense = hamiltonian.J1J2.connected_dense
+
+    def every_bond(self, c):
+        d, H = dense(self, c)
+        if self.sign_rule:
+            nnn = np.array([b[2] for b in self.bonds])
+            H[:, nnn] = -H[:, nnn]
+        return d, H
+    monkeypatch.setattr(hamiltonian.J1J2, 'connected_dense', every_bond)
+    _fails(cnn_pins.test_full_enumeration_identity_j1j2, setup, True)
+
+
 def test_zero_doping_diagonal_without_quarter(monkeypatch):
     """t-J diagonal J s_i s_j / 4 without the - J n_i n_j / 4 term: the
     zero-doping identity with the shifted Heisenberg energy fails."""
@@ -66,6 +85,19 @@ def test_silu_derivative_missing_term(monkeypatch):
     """silu'(z) taken as sigmoid(z): the finite-difference check of the
     backward fails."""
     monkeypatch.setattr(cnn, 'silu_grad', cnn.sigmoid)
+    _fails(cnn_pins.test_backward_matches_central_differences, 4, 1, 4, 2, 8, 8)
+
+
+def test_phase_head_reads_the_amplitude_weights(monkeypatch):
+    """phi = w_a . hbar (the head's weight blocks mixed up): the
+    finite-difference check finds d phi / d w_phi = 0 where the backward
+    says hbar."""
+    unpack = cnn.unpack
+
+    def mixed(params, spec):
+        layers, w_a, _ = unpack(params, spec)
+        return layers, w_a, w_a
+    monkeypatch.setattr(cnn, 'unpack', mixed)
     _fails(cnn_pins.test_backward_matches_central_differences, 4, 1, 4, 2, 8, 8)
 
 
