@@ -431,18 +431,19 @@ def run_reference(args):
     line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 'samples/s', 'n_gpus': 0,
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1000 * total / len(times),
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
-            'data': 'synthetic', 'config': _config(w, args.workload, 'oracle'),
+            'data': 'synthetic', 'config': _config(w, args.workload),
             'cpu_baseline': {'value': value, 'unit': 'samples/s', 'cores': cores, 'kind': 'oracle',
                              'sample': '%d uniform random sector configurations per step, E_loc only' % per_step},
             'e2e': {'value': value, 'unit': 'samples/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
     print(json.dumps(line), flush=True)
 
 
-def _config(w, wname, precision):
+def _config(w, wname):
+    """The workload, identical on both arms (the arithmetic type is the line's dtype)."""
     return {'workload': '%s: %s %dx%d, %d conv layers x %d channels, %d samples / %d chains' % (
         wname, 'J1-J2 (J2=0.5)' if w['model'] == 'j1j2' else 't-J (t=1, J=0.4)', w['L'], w['L'], w['n_layers'],
         w['channels'], w['n_samples'], w['n_chains']),
-        'precision': precision, 'n_samples': w['n_samples'], 'n_chains': w['n_chains'],
+        'n_samples': w['n_samples'], 'n_chains': w['n_chains'],
         'lattice': '%dx%d' % (w['L'], w['L']), 'sr': {'eps': 1e-4, 'rtol': 1e-8, 'lr': 0.02},
         'l2': 'flushed (256 MB write) before every timed step', 'parallelism': 'replicas'}
 
@@ -646,7 +647,7 @@ def main():
             'metric': METRIC, 'value': value, 'unit': 'samples/s', 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': float(step_total_ms / args.steps), 'higher_is_better': True,
             'scaling': 'weak', 'vs_baseline': None, 'dtype': args.precision, 'data': 'synthetic',
-            'config': _config(w, args.workload, args.precision),
+            'config': _config(w, args.workload),
             'sr_steps_per_s': sr_steps_per_s,
             'latency_ms': {'p50': float(np.percentile(step_ms, 50)), 'p99': float(np.percentile(step_ms, 99))},
             'stage_ms': {k: float(stage[:, i].mean()) for i, k in enumerate(['sample', 'eloc', 'grad', 'sr'])},
