@@ -148,10 +148,13 @@ def test_sampler_mixes_from_a_common_start(exact_4x4):
     assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-3
 
 
-def test_sampler_chi_square_tj_sector():
+@pytest.mark.parametrize('start', ['uniform', 'packed'])
+def test_sampler_chi_square_tj_sector(start):
     """t-J 4x4 with 2 up, 2 down and 12 holes (10,920 states): hops and
     exchanges sample the enumerated |psi|^2, and the same counts reject
-    |psi|^1."""
+    |psi|^1. 'uniform': independent uniform starts; 'packed': every chain
+    starts with the four electrons on one 2x2 plaquette (up up / down down),
+    so the chains must spread them over the lattice."""
     spec = cnn.NetSpec(4, 3, 4, 2)
     params = nqs_synth.random_params(3, 4, 2, seed=24, scale=2.0)
     basis = ed.sector_basis(16, 2, 2)
@@ -161,7 +164,13 @@ def test_sampler_chi_square_tj_sector():
     p /= p.sum()
     assert p.max() / p.min() > 100.0
     n_ch = 4096
-    ch0 = sampler.init_chains(4, n_ch, sampler.canonical_values(16, 2, 2))
+    if start == 'uniform':
+        ch0 = sampler.init_chains(4, n_ch, sampler.canonical_values(16, 2, 2))
+    else:
+        packed = np.zeros(16, dtype=np.int8)
+        packed[[0, 1]] = 1
+        packed[[4, 5]] = -1
+        ch0 = np.tile(packed, (n_ch, 1))
     samples = sampler.metropolis(params, spec, ch0, 0, 4, 1, 1, 40)[0]
     obs, exp_p, bins = _binned_counts(samples, basis, p)
     chi2 = ((obs - n_ch * exp_p) ** 2 / (n_ch * exp_p)).sum()
