@@ -286,7 +286,10 @@ def eloc_algorithmic_flops(w, n_samples, pairs, n_conn):
 
 
 TRAFFIC_SOURCES = ('tc.cu', 'tc_ptx.cuh', 'common.cuh', 'internal.h')
-TRAFFIC_PROFILE = os.path.join(ROOT, 'profiles', 'eloc_tc_j1j2_10x10.md')
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one E_loc launch captured by ncu under
+# `bench.py --profile-eloc 2048`, with the hash of the kernel sources it was taken on
+TRAFFIC_RECORD = {'kernel': 'eloc_tc_kernel', 'samples': 2048, 'dram_bytes': 1811456,
+                  'source_sha256': '535bb2c0dbb03e751350b43c4e7c8151a5f913d06ede107b567cdfba83323b8b'}
 
 
 def kernel_source_hash():
@@ -300,19 +303,11 @@ def kernel_source_hash():
 
 def recorded_traffic(n_samples):
     """DRAM bytes (read + write) of one E_loc launch of n_samples, scaled
-    from the ncu capture recorded in the profile summary, or None if there is
-    no record or the kernel sources changed since it was taken."""
-    try:
-        with open(TRAFFIC_PROFILE) as f:
-            for line in f:
-                if line.startswith('traffic-record:'):
-                    kv = dict(t.split('=', 1) for t in line.split(':', 1)[1].split())
-                    if kv.get('source_sha256') != kernel_source_hash():
-                        return None
-                    return float(kv['dram_bytes']) * n_samples / float(kv['samples'])
-    except (OSError, ValueError, KeyError):
+    linearly from TRAFFIC_RECORD, or None once the kernel sources differ from
+    the ones the record was taken on."""
+    if TRAFFIC_RECORD['source_sha256'] != kernel_source_hash():
         return None
-    return None
+    return float(TRAFFIC_RECORD['dram_bytes']) * n_samples / float(TRAFFIC_RECORD['samples'])
 
 
 def load_peaks():
@@ -621,8 +616,8 @@ def main():
                                    'frac': flops_dense / eloc_launch_s / 1e12 / peak}}
             if w['channels'] == 16:
                 # context: the rate of back-to-back M128 N16 K16 MMAs (39.1 cycles each, bound by the shared-memory
-                # operand path; measured by paper_2204_07816_gb300/microbench/mma_rate.cu) at the clock seen: the
-                # ceiling of one MMA per 3x3 tap with 16 channels
+                # operand path, measured with a clock64 probe on GB300) at the clock seen: the ceiling of one MMA
+                # per 3x3 tap with 16 channels
                 mhz = (clocks or {}).get('sm_mhz') or peaks.get('sm_max_mhz', 2070.0)
                 n16 = 152 * (2.0 * 128 * 16 * 16 / 39.1) * mhz * 1e6 / 1e12
                 roof['mma_n16_ceiling'] = {'peak': n16, 'frac': achieved / n16,

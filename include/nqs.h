@@ -246,16 +246,21 @@ int nqs_logpsi_grad(nqs_ctx *ctx, const int8_t *configs, int64_t n, double *O_ou
  * application that owns all device memory through its own allocator, or a
  * framework that forbids allocations from libraries while it records work),
  * and that therefore cannot create an nqs_ctx either.
- * It computes exactly what nqs_logpsi_grad computes (same kernel; output
- * O_out device float64 [2n][P], real-stacked as there), for the problem p,
- * the device float64 parameters `params` and the device int8 configurations
- * [n][N], enqueued on `stream` (cudaStream_t, NULL = legacy default stream)
- * of the current device.
+ * It runs the kernels nqs_logpsi_grad runs for the same precision
+ * (NQS_FP64: the float64 backward; NQS_FP32 and NQS_BF16: the float32
+ * shared-memory backward for 16 or 32 channels, else the plain float32
+ * one), so O_out (device float64 [2n][P], real-stacked as there) is
+ * bitwise the same, for the problem p, the device float64 parameters
+ * `params` and the device int8 configurations [n][N], enqueued on `stream`
+ * (cudaStream_t, NULL = legacy default stream) of the current device. Its
+ * grid holds only as many blocks as have working arrays in the fixed array,
+ * so large problems run on fewer SMs, and slower, than nqs_logpsi_grad.
  * Working memory: one fixed device array of 8 MiB that the library defines
  * at file scope (every GPU that loads the library holds it until the
  * process exits). The call rejects, with NQS_ERR_UNSUPPORTED, problems
  * whose per-block working arrays (plus a float32 copy of the parameters
- * for NQS_FP32 / NQS_BF16) do not fit in it. All calls share the array and
+ * for NQS_FP32 / NQS_BF16) do not fit in it, and devices with an ordinal of
+ * 64 or more. All calls share the array and
  * it keeps the last call's contents; calls that overlap on the same GPU
  * (issued on two streams, or from two host threads) race on it, so the
  * caller must serialise them. Each GPU has its own copy of the array.
@@ -278,7 +283,10 @@ const char *nqs_noalloc_last_error(void);
  * (relative residual) and energy_out ([2]: Re, Im of <E>) are HOST
  * pointers, written before the call returns (the call waits for the
  * stream). Returns NQS_ERR_NOT_CONVERGED (delta and the update still
- * applied) when max_iter is reached first. */
+ * applied) when max_iter is reached first, and NQS_ERR_NONFINITE when the
+ * force, the residual or the energy is not finite (a NaN or Inf in O or
+ * eloc); the parameters are then left unchanged even if apply_update is
+ * set. */
 int nqs_sr_solve(nqs_ctx *ctx, const double *O, const double *eloc, int64_t n, double eps, double rtol,
                  int32_t max_iter, double lr, double *delta_out, int32_t *iters_out, double *resid_out,
                  double *energy_out, int32_t apply_update);

@@ -616,10 +616,10 @@ int launch_bounds_probe(const LaunchEnv &env) {
 
 // ------------------------------------------------------------------ allocation-free local derivatives
 // Some callers cannot allocate device memory: code running where cudaMalloc
-// is not allowed (inside a stream capture of a larger graph, under an
-// allocator that forbids foreign allocations, or in a process that manages
-// all device memory itself). nqs_logpsi_grad_noalloc serves them: it runs
-// the same per-sample backward kernel, with its per-block working arrays in
+// is not allowed (under an allocator that forbids foreign allocations, or in
+// a process that manages all device memory itself). nqs_logpsi_grad_noalloc
+// serves them: it runs the per-sample backward kernels of nqs_logpsi_grad,
+// with their per-block working arrays in
 // a fixed device array that the library defines at file scope, so the call
 // itself allocates nothing. Every GPU that loads the library holds this
 // array until the process exits. All calls share it and it keeps the last
@@ -671,21 +671,33 @@ extern "C" int nqs_logpsi_grad_noalloc(const nqs_problem *q, const double *param
     p.n_bonds = (q->model == NQS_MODEL_J1J2 ? 4 : 2) * p.N;
     p.n_up = q->n_up;
     p.n_down = q->n_down;
-    // the bf16 precision differentiates with float32 internals, as nqs_logpsi_grad does
+    // the bf16 precision differentiates with float32 internals, as nqs_logpsi_grad does; like it, float32 runs
+    // grad_fast_kernel (shared-memory working sets, per-block float32 scratch) where that kernel supports the
+    // problem, else the plain float kernel
     const bool f64 = precision == NQS_FP64;
-    const size_t esz = f64 ? 8 : 4;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        g_noalloc_error = "device " + std::to_string(dev) + " is beyond the " + std::to_string(kNoAllocMaxDevices) +
+                          " devices the allocation-free entry point serves";
+        return NQS_ERR_UNSUPPORTED;
+    }
+    int num_sms = 0, optin = 0;
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) { g_noalloc_error = cudaGetErrorString(e); return NQS_ERR_CUDA; }
+    const bool fast = !f64 && grad_fast_supported(p, (size_t)optin);
     const size_t params_bytes = f64 ? 0 : align16((size_t)P * 4);
-    const size_t per_block = grad_per_block(p) * esz;
+    // per-block float / double working arrays of the kernel that runs
+    const size_t per_block = fast ? grad_fast_scratch_bytes(p, 1) : grad_per_block(p) * (f64 ? 8 : 4);
     if (params_bytes + per_block > kNoAllocScratchBytes) {
         g_noalloc_error = "problem needs " + std::to_string(params_bytes + per_block) +
                            " bytes of working memory; the fixed array holds " + std::to_string(kNoAllocScratchBytes);
         return NQS_ERR_UNSUPPORTED;
-    }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
-        g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
-        return NQS_ERR_CUDA;
     }
     void *base = nullptr;
     {
@@ -703,13 +715,30 @@ extern "C" int nqs_logpsi_grad_noalloc(const nqs_problem *q, const double *param
         }
         base = g_noalloc_ptr[dev];
     }
-    int num_sms = 0;
-    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) { g_noalloc_error = cudaGetErrorString(e); return NQS_ERR_CUDA; }
     const cudaStream_t s = (cudaStream_t)stream;
-    const int64_t fit = (int64_t)((kNoAllocScratchBytes - params_bytes) / per_block);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n, fit), (int64_t)num_sms * 2));
     unsigned char *scratch = static_cast<unsigned char *>(base) + params_bytes;
+    const size_t scratch_bytes = kNoAllocScratchBytes - params_bytes;
+    if (fast) {
+        float *p32 = static_cast<float *>(base);
+        convert_params_kernel<<<(p.P + 255) / 256, 256, 0, s>>>(params, p32, p.P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { g_noalloc_error = std::string("launch: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }
+        // the fast kernel's launcher sizes its grid by the blocks whose scratch fits in the array
+        int64_t launches = 0;
+        std::string msg;
+        LaunchEnv env;
+        env.stream = s;
+        env.num_sms = num_sms;
+        env.max_smem = (size_t)optin;
+        env.err = nullptr;
+        env.launches = &launches;
+        env.msg = &msg;
+        const int rc = launch_grad_fast(p, p32, params, configs, n, O_out, scratch, scratch_bytes, env);
+        if (rc) g_noalloc_error = msg;
+        return rc;
+    }
+    const int64_t fit = (int64_t)(scratch_bytes / per_block);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n, fit), (int64_t)num_sms * 2));
     if (f64) {
         grad_plain_kernel<double><<<blocks, kThreads, 0, s>>>(p, params, params, configs, n, O_out,
                                                                reinterpret_cast<double *>(scratch), grad_per_block(p));

@@ -572,15 +572,17 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     if (iters_out) *iters_out = iters;
     if (resid_out) *resid_out = resid;
     if (energy_out) { energy_out[0] = host_sc[S_ERE]; energy_out[1] = host_sc[S_EIM]; }
+    // a non-finite force, residual or energy (a NaN or Inf in O or E_loc) means delta is not a step: the
+    // parameters are left as they are
+    if (!std::isfinite(fnorm) || !std::isfinite(resid) || !std::isfinite(host_sc[S_ERE])) {
+        *env.msg = "SR: non-finite force, residual or energy (parameters not updated)";
+        return NQS_ERR_NONFINITE;
+    }
     if (apply) {
         update_kernel<<<(P + 255) / 256, 256, 0, s>>>(params, delta, P, lr);
         ++*env.launches;
     }
     if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR update launch failed"; return NQS_ERR_CUDA; }
-    if (!std::isfinite(resid) || !std::isfinite(host_sc[S_ERE])) {
-        *env.msg = "SR: non-finite residual or energy";
-        return NQS_ERR_NONFINITE;
-    }
     if (fnorm > 0.0 && resid > rtol) {
         *env.msg = "SR: conjugate gradient reached max_iter before the tolerance";
         return NQS_ERR_NOT_CONVERGED;

@@ -284,3 +284,29 @@ def test_sr_not_converged_status():
     _, info = ctx.sr_solve(dev(np.concatenate([dA, dPhi], 0)), dev(np.stack([e.real, e.imag], 1)), rtol=1e-14,
                            max_iter=1)
     assert not info['converged'] and info['iters'] == 1
+
+
+@pytest.mark.parametrize('where', ['O', 'eloc'])
+def test_sr_nonfinite_input_leaves_params_unchanged(where):
+    # a NaN in O (or E_loc) makes the solve non-finite: NQS_ERR_NONFINITE, and apply_update must not write
+    # the NaN step into the parameters
+    w = WL['j1j2_4x4']
+    ctx, params = make_ctx(w, param_seed=37)
+    spec, ham = oracle_of(w)
+    cfg = configs_for(w, 128, seed=38)
+    _, _, dA, dPhi = cnn.backward(params, cfg, spec)
+    e = eloc.local_energy_batch(params, cfg, spec, ham)
+    O = np.concatenate([dA, dPhi], 0)
+    E = np.stack([e.real, e.imag], 1)
+    if where == 'O':
+        O[5, 7] = np.nan
+    else:
+        E[3, 0] = np.nan
+    before = ctx.params.clone()
+    nqs = lib()
+    with pytest.raises(nqs.NQSError) as ei:
+        ctx.sr_solve(dev(O), dev(E), eps=1e-3, rtol=1e-10, lr=0.05, apply_update=True)
+    assert ei.value.code == -4
+    torch.cuda.synchronize()
+    assert torch.equal(ctx.params, before)
+
