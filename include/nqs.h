@@ -93,10 +93,12 @@ int64_t nqs_param_count(const nqs_problem *p);
  * opt-in shared memory per block (host only, no GPU work; the launchers use
  * the same code with the current device's values). kind: 0 = nqs_logpsi,
  * 1 = nqs_local_energy (n = samples), 2 = nqs_sample (n = chains).
- * out: host int32 [8] = configurations per group (G), groups in flight per
+ * out: host int32 [9] = configurations per group (G), groups in flight per
  * block, blocks per SM the plan is sized for, epilogue warps, 128-row tiles
  * per group, shared-memory bytes per block, tensor-memory columns per block,
- * grid size. Returns NQS_ERR_INVALID_ARG for a bad problem or argument,
+ * grid size, form (0: one MMA per 3x3 tap and 128-row tile of padded
+ * positions; 1: the local energy's row form, rows = (lattice row,
+ * configuration) and x positions along tensor-memory columns). Returns NQS_ERR_INVALID_ARG for a bad problem or argument,
  * NQS_ERR_UNSUPPORTED if the tensor-core path cannot run p (channels other
  * than 16 or 32, or no plan fits). */
 int nqs_tc_plan(const nqs_problem *p, int32_t kind, int64_t n, int32_t max_smem_per_block, int32_t num_sms,

@@ -68,9 +68,22 @@ struct TcPlan {
     // packed parameter image (global): fp32 biases + head, then bf16 operand
     // images of layer 0 (K0 x C) and of every later layer (9 x C x C)
     uint32_t f32_count, f32_bytes;
-    // shared-memory offsets; act holds slots x 2 buffers of act_bytes
+    // shared-memory offsets; act holds slots x 2 buffers of act_bytes (row form: one buffer)
     uint32_t o_act, o_w0, o_w1, o_f32, o_rowtab, o_sitetab, o_spad, o_spins, o_res, o_bar, o_extra, total;
+    // row form (rows = 1, local energies): activations [kc][(xp * Lp + yp) * G + g][16 B] updated in place,
+    // rows_total rows per plane; a 4 KB zero block; the MMA lists; the layer images of layers >= 1 sit wimg
+    // bytes after the tap-form images
+    int rows, rows_total;
+    uint32_t wimg, o_zero, o_mtab;
 };
+
+// Row form: per issuer, the MMAs of a layer >= 1 (kMtabLayer entries at
+// most) and of layer 0 (kMtab0), precomputed at bind time:
+// {A descriptor low word, B descriptor low word relative to the weight
+// buffer, TMEM column, instruction descriptor}. Both descriptors' high words
+// are the same for every entry (SBO = 128 bytes, tcgen05 version bit).
+constexpr int kMtabLayer = 64, kMtab0 = 32;
+constexpr uint32_t kMtabBytes = 16u * kIssuers * (kMtabLayer + kMtab0) + 16u * kIssuers;   // + counts
 
 __host__ __device__ inline uint32_t al16(uint32_t v) { return (v + 15u) & ~15u; }
 
@@ -155,7 +168,7 @@ __device__ __forceinline__ uint32_t act_addr(const TcPlan &pl, const TcShared &s
 }
 
 __device__ __forceinline__ const unsigned char *tc_layer_weights(const TcPlan &pl, const unsigned char *packed, int l) {
-    return packed + pl.f32_bytes + (l == 0 ? 0 : pl.w0bytes + (size_t)(l - 1) * pl.wbytes);
+    return packed + pl.f32_bytes + (l == 0 ? 0 : pl.w0bytes + pl.wimg + (size_t)(l - 1) * pl.wbytes);
 }
 
 // Issue the bulk copy of weight-load number q (layer (q - wbase) mod n_layers).
@@ -176,6 +189,21 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, co
     for (long long it = 0; it < limit; ++it) {
         if (ptx::mbar_try_wait(bar, parity)) return true;
         if ((it & 255) == 255 && *(volatile const int *)abort_flag) return false;
+    }
+    return false;
+}
+
+// Wait on an mbarrier phase the tensor core completes after many cycles (a
+// layer's or a tile's MMAs): sleeping try_waits instead of polling, so the
+// waiting epilogue warps leave the issue slots to the warps that work.
+// Gives up when another thread raised the abort flag or after the time limit.
+__device__ __forceinline__ bool wait_sleep_or_abort(uint64_t *bar, uint32_t parity, const int *abort_flag) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    for (long long it = 0; it < ptx::kWaitLimit; ++it) {
+        if (ptx::mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (*(volatile const int *)abort_flag) return false;
+        if (ptx::globaltimer_ns() - t0 > ptx::kSleepWaitLimitNs) return false;
     }
     return false;
 }
@@ -393,7 +421,7 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
     for (int t = t0 + (warp >> 2); warp < pl.epi && t < t1; t += pl.epi / 4) {
         const uint32_t parity = (st.tphase >> (slot * kMaxTiles + t)) & 1u;
         const uint2 dst = sh.rowtab[t * 128 + quarter * 32 + lane];
-        const bool got = wait_or_abort(&sh.bar_tile[slot * kMaxTiles + t], parity, sh.abort_flag);
+        const bool got = wait_sleep_or_abort(&sh.bar_tile[slot * kMaxTiles + t], parity, sh.abort_flag);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // reconverges the warp
         ptx::tc_fence_after();
         uint32_t r[C / 16][16];
@@ -464,10 +492,9 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
 }
 
 // a[g] = sum over sites of the head contributions (one warp per g, fixed order).
-__device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const int *roll) {
+// contrib: [a | phi][g][padded position], as the last layer's epilogue stores them.
+__device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const int *roll, const float *contrib) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G, Lp2 = pl.Lp * pl.Lp;
-    const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act +
-                                                           (uint32_t)(slot * 2 + ((pl.n_layers - 1) & 1)) * pl.act_bytes);
     double *res = sh.res + slot * 2 * G;
     for (int g = warp; g < G; g += (int)(blockDim.x >> 5)) {
         float sa = 0.f, sp = 0.f;
@@ -513,8 +540,345 @@ __device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned 
         for (int s = 0; s < pl.slots; ++s) {
             if (!epilogue_layer<C>(pl, sh, st, s, l, err, band, cache, s == 0 ? cache_w : nullptr)) return false;
             if (l + 1 < pl.n_layers) issue_layer<C>(pl, sh, packed, st, s, l + 1, err, band);
-            else head_slot(pl, sh, s, band.roll);
+            else head_slot(pl, sh, s, band.roll,
+                           reinterpret_cast<const float *>(sh.base + pl.o_act +
+                                                           (uint32_t)(s * 2 + ((pl.n_layers - 1) & 1)) * pl.act_bytes));
         }
+    }
+    st.wseq += (uint32_t)pl.n_layers;
+    return true;
+}
+
+// ---------------------------------------------------------------- row form (local energies)
+// The tap form above issues one N = C MMA per 3x3 tap and output tile, so
+// every A byte (128 rows x 16 channels) feeds only C MACs and the shared-
+// memory operand path bounds it. The row form lays a group's activations out
+// as rows m = y * G + g (lattice row, configuration) and puts the x positions
+// along tensor-memory columns: D[m][x * C + c]. For one padded input column
+// xp and one kernel row dy, a single MMA with N = 3C (the three dx taps'
+// weights side by side) writes its three column blocks onto the outputs
+// x = xp - 2, xp - 1, xp (the TMEM column offset does the dx shift), so an
+// A operand serves 3C outputs per row. Per layer: one zeroing MMA per issuer,
+// then 3 (dy) x (L + 2) (xp) MMAs. Each output still accumulates its taps in
+// the tap form's order (dy, then dx, then the K halves), onto a zeroed
+// accumulator. Layer 0 keeps the tap form's 9-tap im2col (K = 16 or 32,
+// N = C) per x. All MMAs of a layer complete before its epilogue writes, so
+// one activation buffer is updated in place. The two issuing warps take the
+// left and right halves of the output columns (disjoint accumulators); the
+// epilogue warps take a TMEM lane quarter and half of the columns each.
+
+__device__ __forceinline__ uint32_t row_act(const TcPlan &pl, const TcShared &sh) {
+    return ptx::smem_u32(sh.base + pl.o_act);
+}
+
+// Low 32 bits of a no-swizzle smem descriptor (start address and LBO, both
+// in 16-byte units); the high word is kDescHi for every operand here.
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr, uint32_t lbo) {
+    return ((saddr & 0x3FFFFu) >> 4) | (((lbo & 0x3FFFFu) >> 4) << 16);
+}
+constexpr uint32_t kDescHi = (128u >> 4) | (1u << 14);   // SBO = 128 B; bit 46: descriptor version
+
+// Issuer iw's MMA lists (called by the issuer lane at bind time). Layer >= 1:
+// per kernel row dy and input column xp in [xa, xb + 1], the outputs
+// lo .. hi = max(xp - 2, xa) .. min(xp, xb - 1) with weight blocks from
+// j0 = 2 - xp + lo, K halves innermost: every output sees its taps in the
+// tap form's order (dy, then dx, then K).
+template <int C>
+__device__ void row_build_mtab(const TcPlan &pl, const TcShared &sh, int iw) {
+    uint4 *tab = reinterpret_cast<uint4 *>(sh.base + pl.o_mtab) + iw * (kMtabLayer + kMtab0);
+    int *cnt = reinterpret_cast<int *>(sh.base + pl.o_mtab + 16u * kIssuers * (kMtabLayer + kMtab0)) + 2 * iw;
+    const uint32_t act = row_act(pl, sh);
+    const int xa = iw * pl.L / kIssuers, xb = (iw + 1) * pl.L / kIssuers;
+    constexpr int KC = C / 8;
+    int n = 0;
+    for (int dy = 0; dy < 3; ++dy)
+        for (int xp = xa; xp <= xb + 1; ++xp) {
+            const int lo = max(xp - 2, xa), hi = min(xp, xb - 1);
+            const int j0 = 2 - xp + lo;
+            const uint32_t arow = (uint32_t)((xp * pl.Lp + dy) * pl.G);
+            for (int kk = 0; kk < C / 16; ++kk) {
+                const uint32_t boff = (uint32_t)(((dy * KC + 2 * kk) * 3 * C + j0 * C) * 16);
+                tab[n++] = make_uint4(desc_lo(act + arow * 16u + (uint32_t)(2 * kk) * pl.plane, pl.plane),
+                                      desc_lo(boff, 3 * C * 16), (uint32_t)(lo * C),
+                                      ptx::idesc_bf16(128, (hi - lo + 1) * C));
+            }
+        }
+    cnt[0] = n;
+    int n0 = 0;
+    for (int x = xa; x < xb; ++x)
+        for (int kk = 0; kk < pl.K0 / 16; ++kk)
+            tab[kMtabLayer + n0++] = make_uint4(desc_lo(act + (uint32_t)x * 128u * 16u + (uint32_t)(2 * kk) * pl.plane,
+                                                        pl.plane),
+                                                desc_lo((uint32_t)(2 * kk * C * 16), C * 16),
+                                                (uint32_t)(x * C) | (kk ? 0x80000000u : 0u), ptx::idesc_bf16(128, C));
+    cnt[1] = n0;
+}
+
+// Spins of the group to the layer-0 im2col: row x * 128 + m (m = y * G + g),
+// K0 columns tap-major (one-hot channel minor), as build_slot writes them.
+// Threads 0 .. 255 each keep one accumulator row m and walk every other
+// column x; the 3 x 3 neighbourhood comes from the row's three lattice rows.
+__device__ void build_rows(const TcPlan &pl, const TcShared &sh) {
+    const int G = pl.G, N = pl.N, L = pl.L;
+    const uint32_t a0 = row_act(pl, sh);
+    const uint32_t one = 0x3F80u, minus_one = 0xBF80u;   // bf16 +1, -1
+    if (threadIdx.x < 256) {
+        const int m = threadIdx.x & 127;
+        const bool valid = m < G * L;
+        const int y = valid ? m / G : 0, g = valid ? m - y * G : 0;
+        const int8_t *sp = sh.spins + g * N;
+        const int yr[3] = {(y == 0 ? L - 1 : y - 1) * L, y * L, (y == L - 1 ? 0 : y + 1) * L};
+        for (int x = (int)(threadIdx.x >> 7); x < L; x += 2) {
+            uint32_t w[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) w[i] = 0u;
+            if (valid) {
+                const int xc[3] = {x == 0 ? L - 1 : x - 1, x, x == L - 1 ? 0 : x + 1};
+                int sv[9];
+#pragma unroll
+                for (int o = 0; o < 9; ++o) sv[o] = sp[yr[o / 3] + xc[o % 3]];
+#pragma unroll
+                for (int o = 0; o < 9; ++o) {
+                    const int sval = sv[o];
+                    if (pl.c_in == 1) {
+                        const uint32_t b = sval > 0 ? one : minus_one;
+                        w[o >> 1] |= b << (16 * (o & 1));
+                    } else {
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            const int k = 3 * o + ch;
+                            const bool hit = ch == 0 ? sval == 0 : (ch == 1 ? sval == 1 : sval == -1);
+                            if (hit) w[k >> 1] |= one << (16 * (k & 1));
+                        }
+                    }
+                }
+            }
+            const uint32_t row = (uint32_t)(x * 128 + m);
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc)
+                if (kc < pl.K0 / 8)
+                    ptx::st_shared_v4(a0 + kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1], w[4 * kc + 2],
+                                      w[4 * kc + 3]);
+        }
+    }
+    ptx::fence_async_smem();
+    __syncthreads();
+}
+
+// Issue layer l's MMAs (issuer threads only): issuer iw owns output columns
+// x in [iw L / kIssuers, (iw + 1) L / kIssuers) and commits to bar_tile[iw].
+template <int C>
+__device__ void row_issue(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int l,
+                          int *err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t q = st.wseq + (uint32_t)l;
+    const int iw = warp - pl.epi;
+    if (lane == 0 && iw >= 0 && iw < kIssuers) {
+        if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
+            if (iw == 0) issue_weight_load(pl, sh, packed, q + 1, st.wbase);
+            ptx::tc_fence_after();
+            const uint32_t tmem = *sh.tmem_addr;
+            const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
+            const uint4 *tab = reinterpret_cast<const uint4 *>(sh.base + pl.o_mtab) + iw * (kMtabLayer + kMtab0);
+            const int *cnt = reinterpret_cast<const int *>(sh.base + pl.o_mtab +
+                                                           16u * kIssuers * (kMtabLayer + kMtab0)) + 2 * iw;
+            const uint32_t wlo = wb >> 4;   // weight buffer start in 16-byte units, added to the B entries
+            if (l == 0) {
+                const int n0 = cnt[1];
+                for (int k = 0; k < n0; ++k) {
+                    const uint4 e = tab[kMtabLayer + k];
+                    ptx::mma_bf16(tmem + (e.z & 0x7FFFFFFFu), ((uint64_t)kDescHi << 32) | e.x,
+                                  ((uint64_t)kDescHi << 32) | (e.y + wlo), e.w, e.z >> 31);
+                }
+            } else {
+                // zero this issuer's accumulators: A = B = the zero block, N = its columns
+                const int xa = iw * pl.L / kIssuers, xb = (iw + 1) * pl.L / kIssuers;
+                const uint64_t z = ((uint64_t)kDescHi << 32) | desc_lo(ptx::smem_u32(sh.base + pl.o_zero), 2048);
+                ptx::mma_bf16(tmem + (uint32_t)(xa * C), z, z, ptx::idesc_bf16(128, (xb - xa) * C), 0u);
+                const int n = cnt[0];
+#pragma unroll 4
+                for (int k = 0; k < n; ++k) {
+                    const uint4 e = tab[k];
+                    ptx::mma_bf16(tmem + e.z, ((uint64_t)kDescHi << 32) | e.x, ((uint64_t)kDescHi << 32) | (e.y + wlo),
+                                  e.w, 1u);
+                }
+            }
+            ptx::mma_commit(&sh.bar_tile[iw]);
+        } else {
+            raise_abort(sh, err);
+        }
+    }
+    st.wissued = q + 2;
+}
+
+// TMEM columns [col, col + C) of this warp's lane quarter into r (no wait).
+template <int C>
+__device__ __forceinline__ void row_ld(uint32_t taddr, uint32_t (&r)[C / 16][16]) {
+#pragma unroll
+    for (int hh = 0; hh < C / 16; ++hh) ptx::tmem_ld16_nowait(taddr + (uint32_t)(16 * hh), r[hh]);
+}
+template <int C>
+__device__ __forceinline__ void row_wait(uint32_t (&r)[C / 16][16]) {
+    ptx::tmem_wait_ld();
+#pragma unroll
+    for (int hh = 0; hh < C / 16; ++hh) ptx::reg_fence16(r[hh]);
+}
+
+// One output column x of one row (y, g): bias + SiLU to bf16, stored at the
+// padded position and its periodic images; or, after the last layer, the
+// head contributions of the position.
+template <int C>
+__device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *contrib, const float *bias,
+                                        const float *wa, const float (&hb)[C == 16 ? C : 1], bool last, int x, int y,
+                                        int yimg, int g, const uint32_t (&r)[C / 16][16], int *err) {
+    constexpr int KC = C / 8, HB = C == 16 ? C : 1;
+    const int G = pl.G, L = pl.L, Lp = pl.Lp;
+    float v[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
+    if (!last) {
+        uint32_t w[C / 2];
+#pragma unroll
+        for (int c = 0; c < C / 2; ++c) {
+            const float h0 = C == 16 ? hb[(2 * c) % HB] : 0.5f * bias[2 * c];
+            const float h1 = C == 16 ? hb[(2 * c + 1) % HB] : 0.5f * bias[2 * c + 1];
+            w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
+        }
+        const int ximg = x == 0 ? L + 1 : (x == L - 1 ? 0 : -1);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int xp = a == 0 ? x + 1 : ximg;
+            if (xp < 0) continue;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int yp = b == 0 ? y + 1 : yimg;
+                if (yp < 0) continue;
+                const uint32_t row = (uint32_t)((xp * Lp + yp) * G + g);
+                if (!NQS_INDEX_OK(row < (uint32_t)pl.rows_total, err)) continue;
+#pragma unroll
+                for (int kc = 0; kc < KC; ++kc)
+                    ptx::st_shared_v4(act + (uint32_t)kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1],
+                                      w[4 * kc + 2], w[4 * kc + 3]);
+            }
+        }
+    } else {
+        // the tap form's head arithmetic: c = 0 .. C - 1 in order, 16-byte broadcast loads
+        float ca = 0.f, cp = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < C; c4 += 4) {
+            const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
+            const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
+            const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
+            const float bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {xa.x, xa.y, xa.z, xa.w};
+            const float pp[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float hv = ptx::silu_fast(v[c4 + k] + bb[k]);
+                ca = fmaf(aa[k], hv, ca);
+                cp = fmaf(pp[k], hv, cp);
+            }
+        }
+        // site order [a | phi][g][y * L + x]
+        const int idx = g * pl.N + y * L + x;
+        contrib[idx] = ca;
+        contrib[G * pl.N + idx] = cp;
+    }
+}
+
+// Epilogue of layer l: once every MMA of the layer has completed, bias +
+// SiLU of each output and its bf16 rows (with periodic images) written back
+// into the activation buffer, or after the last layer the head contributions.
+// Each thread walks its columns with the next column's TMEM load in flight.
+template <int C>
+__device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, int l, int *err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
+    const bool last = l == pl.n_layers - 1;
+    const int G = pl.G, L = pl.L;
+    const float *bias = sh.f32 + l * C;
+    const float *wa = sh.f32 + pl.n_layers * C;
+    const uint32_t act = row_act(pl, sh);
+    float *contrib = reinterpret_cast<float *>(sh.base + pl.o_act);
+    bool ok = true;
+    if (warp < pl.epi) {
+        bool got = true;
+        for (int i = 0; i < kIssuers; ++i)
+            got = got && wait_sleep_or_abort(&sh.bar_tile[i], (st.tphase >> i) & 1u, sh.abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+        } else {
+            ptx::tc_fence_after();
+            const uint32_t tmem = *sh.tmem_addr + ((uint32_t)(quarter * 32) << 16);
+            const int m = quarter * 32 + lane;
+            const bool valid = m < G * L;
+            const int y = valid ? m / G : 0, g = valid ? m - y * G : 0;
+            const int yimg = y == 0 ? L + 1 : (y == L - 1 ? 0 : -1);
+            const int nh = pl.epi >> 2, h = warp >> 2;
+            const int x0 = h * L / nh, x1 = (h + 1) * L / nh;
+            float hb[C == 16 ? C : 1];
+#pragma unroll
+            for (int c = 0; c < (C == 16 ? C : 1); ++c) hb[c] = 0.5f * bias[c];
+            uint32_t ra[C / 16][16], rb[C / 16][16];
+            if (x0 < x1) {
+                row_ld<C>(tmem + (uint32_t)(x0 * C), ra);
+                row_wait<C>(ra);
+            }
+            for (int x = x0; x < x1; x += 2) {
+                const bool more = x + 1 < x1;
+                if (more) row_ld<C>(tmem + (uint32_t)((x + 1) * C), rb);
+                if (valid) row_out<C>(pl, act, contrib, bias, wa, hb, last, x, y, yimg, g, ra, err);
+                if (!more) break;
+                row_wait<C>(rb);
+                const bool more2 = x + 2 < x1;
+                if (more2) row_ld<C>(tmem + (uint32_t)((x + 2) * C), ra);
+                if (valid) row_out<C>(pl, act, contrib, bias, wa, hb, last, x + 1, y, yimg, g, rb, err);
+                if (more2) row_wait<C>(ra);
+            }
+        }
+    }
+    if (!ok) raise_abort(sh, err);
+    st.tphase ^= (1u << kIssuers) - 1u;
+    ptx::tc_fence_before();
+    ptx::fence_async_smem();
+    __syncthreads();
+    return *(volatile int *)sh.abort_flag == 0;
+}
+
+// a[g] = sum over sites of the head contributions, stored in site order
+// [a | phi][g][site]: the sites and the reduction tree of head_slot (lane k
+// sums sites k, k + 32, ... in order, then an xor-shuffle tree), so the
+// result is bitwise the tap form's.
+__device__ void row_head(const TcPlan &pl, const TcShared &sh) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G, N = pl.N;
+    const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act);
+    for (int g = warp; g < G; g += (int)(blockDim.x >> 5)) {
+        float sa = 0.f, sp = 0.f;
+        for (int site = lane; site < N; site += 32) {
+            sa += contrib[g * N + site];
+            sp += contrib[G * N + g * N + site];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        }
+        if (lane == 0) {
+            sh.res[g] = (double)sa;
+            sh.res[G + g] = (double)sp;
+        }
+    }
+    __syncthreads();
+}
+
+// Evaluate the group's G configurations (sh.spins) in the row form; results
+// in sh.res. False if a wait timed out (the block must stop).
+template <int C>
+__device__ bool row_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int *err) {
+    build_rows(pl, sh);
+    row_issue<C>(pl, sh, packed, st, 0, err);
+    for (int l = 0; l < pl.n_layers; ++l) {
+        if (!row_epilogue<C>(pl, sh, st, l, err)) return false;
+        if (l + 1 < pl.n_layers) row_issue<C>(pl, sh, packed, st, l + 1, err);
+        else row_head(pl, sh);
     }
     st.wseq += (uint32_t)pl.n_layers;
     return true;
@@ -586,6 +950,44 @@ __device__ void tc_bind(const TcPlan &pl, TcShared &sh, const unsigned char *pac
     for (uint32_t i = threadIdx.x; i < pl.slots * 2 * pl.act_bytes / 4; i += blockDim.x)
         reinterpret_cast<uint32_t *>(smem + pl.o_act)[i] = 0u;
     for (uint32_t i = threadIdx.x; i < (uint32_t)(pl.slots * pl.Lp * pl.Lp * pl.G); i += blockDim.x) sh.spad[i] = 0;
+    ptx::fence_async_smem();
+    __syncthreads();
+    st.wbase = st.wissued;
+    st.wseq = st.wissued;
+    if (threadIdx.x == 0) issue_weight_load(pl, sh, packed, st.wissued, st.wbase);
+    st.wissued += 1;
+}
+
+// Bind the block to a row-form plan: parameters, site and neighbour tables,
+// zeroed activations and zero block, first weight load.
+__device__ void row_bind(const TcPlan &pl, TcShared &sh, const unsigned char *packed, TcState &st) {
+    unsigned char *smem = sh.base;
+    sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
+    sh.spad = nullptr;
+    sh.rowtab = nullptr;
+    sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
+    sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
+    sh.res = reinterpret_cast<double *>(smem + pl.o_res);
+    const float *src = reinterpret_cast<const float *>(packed);
+    for (uint32_t i = threadIdx.x; i < pl.f32_count; i += blockDim.x) sh.f32[i] = src[i];
+    uint2 *sitetab = reinterpret_cast<uint2 *>(smem + pl.o_sitetab);
+    for (int s = threadIdx.x; s < pl.N; s += blockDim.x) {
+        int pos[4];
+        const int n = images(pl.L, pl.Lp, s % pl.L, s / pl.L, pos);
+        sitetab[s] = pack4(pos, n);
+    }
+    // zero the activations (rows no output writes are read only by discarded
+    // accumulator rows, but stay finite) and the zero block
+    for (uint32_t i = threadIdx.x; i < pl.act_bytes / 4; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(smem + pl.o_act)[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < 4096 / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(smem + pl.o_zero)[i] = 0u;
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, iw = warp - pl.epi;
+        if (lane == 0 && iw >= 0 && iw < kIssuers) {
+            if (pl.C == 16) row_build_mtab<16>(pl, sh, iw);
+            else row_build_mtab<32>(pl, sh, iw);
+        }
+    }
     ptx::fence_async_smem();
     __syncthreads();
     st.wbase = st.wissued;
@@ -670,7 +1072,8 @@ __global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) logpsi_tc_kernel(Tc
 // configurations, evaluate sigma and all of them in groups, then
 // E_loc = H_diag + sum_k H_k exp((a'_k - a) + i (phi'_k - phi)) in float64,
 // every term of the sample at once, fixed-order block reduction.
-template <int C>
+// ROWS: the configurations go through the row form (no cones).
+template <int C, bool ROWS = false>
 __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &sh, TcState &st,
                             const unsigned char *packed, const int8_t *cfg, const double *logpsi_s, double *out_s,
                             int *err, unsigned char *cache) {
@@ -691,7 +1094,7 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
     const int recompute = logpsi_s == nullptr;
     // the cone of every connected configuration is evaluated alone when the
     // sample itself is evaluated here (its activations fill the cache)
-    const bool cone = cache != nullptr && recompute && pl.slots == 1;
+    const bool cone = !ROWS && cache != nullptr && recompute && pl.slots == 1;
     for (int r = threadIdx.x; r < N; r += blockDim.x) sigma[r] = cfg[r];
     __syncthreads();
     if (p.model == NQS_MODEL_TJ) snake_prefix(p, sigma, cum, *scr);
@@ -747,25 +1150,36 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
                 roll[c] = r;
             }
             __syncthreads();
-            for (int r = threadIdx.x; r < per * N; r += blockDim.x) {
-                const int c = r / N, site = r - c * N;
-                const int q = e0 + c - lead;   // list position (-1: sigma)
-                int v;
-                if (c >= cnt || q < 0) {
-                    v = sigma[site];
-                } else {
-                    const int k = ord[q];
-                    int s0 = site + roll[c] * L;   // original site: row + roll (mod L)
-                    if (s0 >= N) s0 -= N;
-                    const int i = ci[k], j = cj[k];
-                    v = NQS_INDEX_OK(k >= 0 && k < nconn && i >= 0 && i < N && j >= 0 && j < N && s0 >= 0, err)
-                            ? sigma[s0 == i ? j : (s0 == j ? i : s0)] : 0;
+            // configuration c of the group: one warp per configuration, lanes over sites (no divisions)
+            {
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+                for (int c = warp; c < per; c += nwarps) {
+                    const int q = e0 + c - lead;   // list position (-1: sigma)
+                    const bool own = c >= cnt || q < 0;
+                    const int k = own ? 0 : ord[q];
+                    const int i = own ? -1 : ci[k], j = own ? -1 : cj[k];
+                    const int rl = roll[c] * L;
+                    const bool idx_ok = own || NQS_INDEX_OK(k >= 0 && k < nconn && i >= 0 && i < N && j >= 0 && j < N, err);
+                    int8_t *dst = sh.spins + c * N;
+                    for (int site = lane; site < N; site += 32) {
+                        int v;
+                        if (own) {
+                            v = sigma[site];
+                        } else {
+                            int s0 = site + rl;   // original site: row + roll (mod L)
+                            if (s0 >= N) s0 -= N;
+                            v = idx_ok ? sigma[s0 == i ? j : (s0 == j ? i : s0)] : 0;
+                        }
+                        dst[site] = (int8_t)v;
+                    }
                 }
-                sh.spins[r] = (int8_t)v;
             }
             __syncthreads();
-            if (!tc_forward<C>(pl, sh, packed, st, err, band, cache, (cone && lead && e0 == 0) ? cache : nullptr))
+            if (ROWS) {
+                if (!row_forward<C>(pl, sh, packed, st, err)) return false;
+            } else if (!tc_forward<C>(pl, sh, packed, st, err, band, cache, (cone && lead && e0 == 0) ? cache : nullptr)) {
                 return false;
+            }
             if (threadIdx.x < cnt) {
                 const int c = threadIdx.x, sl = c / G, g = c - sl * G;
                 const int q = e0 + c - lead;
@@ -810,6 +1224,23 @@ __global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>)
     for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
         if (!eloc_sample<C>(pl, p, sh, st, packed, configs + s * p.N, logpsi ? logpsi + 2 * s : nullptr, out + 2 * s,
                             err, my_cache))
+            break;
+    tc_teardown(pl, sh, st);
+}
+
+// Local energies through the row form (plans with L * C <= 256 columns).
+template <int C>
+__global__ void __launch_bounds__(kTcThreads, 2)
+    eloc_rows_kernel(TcPlan pl, Problem p, const unsigned char *packed, const int8_t *configs, const double *logpsi,
+                     int64_t n, double *out, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    TcShared sh;
+    TcState st;
+    tc_init(sh, smem, pl.tmem_cols, st);
+    row_bind(pl, sh, packed, st);
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
+        if (!eloc_sample<C, true>(pl, p, sh, st, packed, configs + s * p.N, logpsi ? logpsi + 2 * s : nullptr,
+                                  out + 2 * s, err, nullptr))
             break;
     tc_teardown(pl, sh, st);
 }
@@ -1024,7 +1455,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
 // fp32 block: biases[l][c], head[2][c]. bf16 block of layer 0: B operand
 // [K0 / 8][C][8] with k = tap (J1-J2) or 3 tap + one-hot channel (t-J),
 // zero for k >= 9 c_in. bf16 block per layer l >= 1: [9][C / 8][C][8],
-// element (tap o, k = c_in, n = c_out).
+// element (tap o, k = c_in, n = c_out); then the same layers again in the
+// row form's order [3][C / 8][3][C][8].
 __global__ void tc_pack_kernel(Problem p, TcPlan pl, const double *params, unsigned char *packed) {
     const int C = p.C;
     float *f = reinterpret_cast<float *>(packed);
@@ -1052,6 +1484,12 @@ __global__ void tc_pack_kernel(Problem p, TcPlan pl, const double *params, unsig
         __nv_bfloat16 *dst =
             reinterpret_cast<__nv_bfloat16 *>(packed + pl.f32_bytes + pl.w0bytes + (size_t)(l - 1) * pl.wbytes);
         dst[((o * (C / 8) + k / 8) * C + n) * 8 + (k % 8)] = __float2bfloat16_rn((float)w);
+        // row-form image of the same layer: [kernel row dy][C / 8][column block j = 1 - dx][C][8], so that
+        // one kernel row's three dx taps are one N = 3C operand
+        __nv_bfloat16 *dr = reinterpret_cast<__nv_bfloat16 *>(packed + pl.f32_bytes + pl.w0bytes +
+                                                               (size_t)(p.n_layers - 1 + l - 1) * pl.wbytes);
+        const int dyi = o / 3, j = 2 - o % 3;
+        dr[(((dyi * (C / 8) + k / 8) * 3 + j) * C + n) * 8 + (k % 8)] = __float2bfloat16_rn((float)w);
     }
 }
 
@@ -1062,6 +1500,83 @@ void plan_weights(const Problem &p, TcPlan &pl) {
     pl.f32_bytes = al16(pl.f32_count * 4);
     pl.w0bytes = (uint32_t)pl.K0 * p.C * 2u;
     pl.wbytes = 9u * p.C * p.C * 2u;
+}
+
+int eloc_extra(const Problem &p);
+
+// Row-form plan (local energies): one group of G = min(16, 128 / L)
+// configurations per block, the L x C accumulator columns of a layer in
+// tensor memory, two blocks per SM. Needs L * C <= 256.
+bool make_row_plan(const Problem &p, size_t max_smem, int extra_bytes, TcPlan *out, std::string *why, int G = 0) {
+    if (p.L * p.C > 256) { *why = "row form needs L * C <= 256 accumulator columns"; return false; }
+    // MMA lists: 3 (dy) x (columns per issuer + 2) x (C / 16) per layer, columns x (K0 / 16) for layer 0
+    const int per_issuer = (p.L + kIssuers - 1) / kIssuers;
+    if (3 * (per_issuer + 2) * (p.C / 16) > kMtabLayer || per_issuer * 2 > kMtab0) {
+        *why = "row form: MMA list too long";
+        return false;
+    }
+    TcPlan pl{};
+    pl.rows = 1;
+    pl.ctas = 2;
+    pl.epi = kMaxEpiWarps;
+    pl.L = p.L;
+    pl.Lp = p.L + 2;
+    pl.N = p.N;
+    pl.G = G > 0 ? std::min(G, 128 / p.L) : std::min(16, 128 / p.L);
+    pl.C = p.C;
+    pl.KC = p.C / 8;
+    pl.c_in = p.c_in;
+    pl.n_layers = p.n_layers;
+    pl.slots = 1;
+    plan_weights(p, pl);
+    pl.wimg = (uint32_t)(p.n_layers - 1) * pl.wbytes;
+    pl.n_tiles = 1;
+    // the last A operand read starts at ((L + 1) Lp + 2) G and spans 128 rows; the im2col of layer 0 takes L x 128
+    pl.rows_total = std::max(pl.Lp * pl.Lp * pl.G + 128, p.L * 128);
+    pl.rows_total = (pl.rows_total + 7) & ~7;
+    pl.rbuf = pl.rows_total;
+    pl.plane = (uint32_t)pl.rows_total * 16u;
+    pl.act_bytes = pl.plane * (uint32_t)std::max(pl.KC, pl.K0 / 8);
+    pl.slot_cols = (uint32_t)(p.L * p.C);
+    uint32_t cols = 32;
+    while (cols < pl.slot_cols) cols <<= 1;
+    pl.tmem_cols = cols;
+    uint32_t o = kBarBytes;
+    pl.o_bar = 0;
+    pl.o_act = o; o = al16(o + pl.act_bytes);
+    pl.o_zero = o; o = al16(o + 4096);
+    pl.o_w0 = o; o = al16(o + pl.wbytes);
+    pl.o_w1 = o; o = al16(o + pl.wbytes);
+    pl.o_f32 = o; o = al16(o + pl.f32_count * 4);
+    pl.o_sitetab = o; o = al16(o + 8 * p.N);
+    pl.o_mtab = o; o = al16(o + kMtabBytes);
+    pl.o_spins = o; o = al16(o + pl.G * p.N);
+    pl.o_res = o; o = al16(o + 16 * pl.G);
+    pl.o_extra = o; o = al16(o + extra_bytes);
+    const uint32_t sm_bytes = 233472u;   // 228 KB per SM, 1 KB reserved per block
+    while (cols * (sm_bytes / (o + 1024u)) > 512u) o += 1024u;
+    pl.total = o;
+    if (cols * 2u > 512u) { *why = "tensor-memory columns do not fit two blocks"; return false; }
+    if (2u * (pl.total + 1024u) > sm_bytes) { *why = "row form: two blocks do not fit the SM's shared memory"; return false; }
+    if (pl.total > max_smem) { *why = "shared memory plan exceeds the per-block limit"; return false; }
+    // the contributions of the head ([2][G][Lp^2] floats) reuse the activation buffer
+    if ((size_t)8 * pl.G * pl.Lp * pl.Lp > pl.act_bytes) { *why = "head contributions exceed the buffer"; return false; }
+    *out = pl;
+    return true;
+}
+
+// Whether the local-energy launch uses the row form (NQS_TC_ROWS=0 turns it
+// off, NQS_TC_ROWS=G forces G configurations per group: tuning and A/B
+// comparisons).
+bool use_row_form(const Problem &p, size_t max_smem, TcPlan *out) {
+    const char *e = getenv("NQS_TC_ROWS");
+    int G = 0;
+    if (e) {
+        G = atoi(e);
+        if (G == 0) return false;
+    }
+    std::string why;
+    return make_row_plan(p, max_smem, eloc_extra(p), out, &why, G);
 }
 
 bool make_plan(const Problem &p, int G, int slots, int ctas, size_t max_smem, int extra_bytes, TcPlan *out,
@@ -1209,7 +1724,7 @@ bool tc_supported(const Problem &p, std::string *why) {
 size_t tc_packed_bytes(const Problem &p) {
     TcPlan pl{};
     plan_weights(p, pl);
-    return pl.f32_bytes + pl.w0bytes + (size_t)(p.n_layers - 1) * pl.wbytes;
+    return pl.f32_bytes + pl.w0bytes + 2 * (size_t)(p.n_layers - 1) * pl.wbytes;   // tap and row images
 }
 
 int launch_tc_pack(const Problem &p, const double *p64, void *packed, const LaunchEnv &env) {
@@ -1256,7 +1771,9 @@ int launch_logpsi_tc(const Problem &p, const double *, const void *packed, const
 size_t tc_eloc_cache_bytes(const Problem &p, size_t max_smem, int num_sms, int64_t n) {
     std::string why;
     TcPlan pl;
-    if (n <= 0 || !tc_supported(p, &why) || !best_plan(p, max_smem, true, 16, 2, &pl, &why)) return 0;
+    if (n <= 0 || !tc_supported(p, &why) || use_row_form(p, max_smem, &pl) ||
+        !best_plan(p, max_smem, true, 16, 2, &pl, &why))
+        return 0;
     const char *d = getenv("NQS_TC_DENSE"), *f = getenv("NQS_TC_CONES");
     const bool force = f && f[0] == '1';
     if (pl.slots != 1 || p.n_layers < 2 || (d && d[0] == '1') || (pl.ctas != 1 && !force)) return 0;
@@ -1270,7 +1787,21 @@ int launch_eloc_tc(const Problem &p, const double *, const void *packed, const i
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
-    if (!tc_supported(p, &why) || !best_plan(p, env.max_smem, true, 16, 2, &pl, &why)) {
+    if (!tc_supported(p, &why)) {
+        *env.msg = why;
+        return NQS_ERR_UNSUPPORTED;
+    }
+    if (use_row_form(p, env.max_smem, &pl)) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * pl.ctas));
+        NQS_TC_DISPATCH(p.C, {
+            auto k = eloc_rows_kernel<CC>;
+            if (int rc = prep(k, pl, env)) return rc;
+            k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, p, (const unsigned char *)packed, configs,
+                                                                        logpsi, n, out, env.err);
+        });
+        return check(env, "eloc_rows_kernel");
+    }
+    if (!best_plan(p, env.max_smem, true, 16, 2, &pl, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
@@ -1395,6 +1926,7 @@ int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int
     bool ok = tc_supported(p, why);
     if (ok) {
         if (kind == 2) ok = sample_plan(p, (int)n, max_smem, num_sms, &pl, why);
+        else if (kind == 1 && use_row_form(p, max_smem, &pl)) ok = true;
         else ok = best_plan(p, max_smem, kind == 1, 16, 2, &pl, why);
     }
     if (!ok) return NQS_ERR_UNSUPPORTED;
@@ -1411,6 +1943,7 @@ int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int
     out[5] = (int32_t)pl.total;
     out[6] = (int32_t)pl.tmem_cols;
     out[7] = (int32_t)grid;
+    out[8] = pl.rows;
     return NQS_OK;
 }
 

@@ -126,7 +126,8 @@ def nqs_param_count(problem):
 
 
 TC_PLAN_KIND = {'logpsi': 0, 'local_energy': 1, 'sample': 2}
-TC_PLAN_FIELDS = ('G', 'slots', 'blocks_per_sm', 'epilogue_warps', 'tiles', 'smem_bytes', 'tmem_cols', 'grid')
+TC_PLAN_FIELDS = ('G', 'slots', 'blocks_per_sm', 'epilogue_warps', 'tiles', 'smem_bytes', 'tmem_cols', 'grid',
+                  'row_form')
 
 
 def tc_plan(problem, kind, n, max_smem_per_block=232448, num_sms=152):
@@ -134,7 +135,7 @@ def tc_plan(problem, kind, n, max_smem_per_block=232448, num_sms=152):
     kind: 'logpsi', 'local_energy' (n = samples) or 'sample' (n = chains).
     Returns a dict of TC_PLAN_FIELDS, or None if the tensor-core path cannot
     run the problem."""
-    out = (ctypes.c_int32 * 8)()
+    out = (ctypes.c_int32 * 9)()
     rc = load().nqs_tc_plan(ctypes.byref(problem), TC_PLAN_KIND[kind], int(n), int(max_smem_per_block), int(num_sms),
                             out)
     if rc == NQS_ERR_UNSUPPORTED:

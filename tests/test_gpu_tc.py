@@ -107,6 +107,7 @@ def test_local_energy_bf16_cones_equal_dense(case, monkeypatch):
     ctx, _ = make_ctx(w, **over)
     n = 24 if over.get('L', w['L']) >= 24 else 48
     cfg = dev(configs_for(w, n, seed=31, **over))
+    monkeypatch.setenv('NQS_TC_ROWS', '0')      # cones belong to the tap form
     monkeypatch.setenv('NQS_TC_CONES', '1')     # also where the plan would not use them by default
     cone = ctx.local_energy(cfg, None, 'bf16')
     monkeypatch.delenv('NQS_TC_CONES')
@@ -117,6 +118,47 @@ def test_local_energy_bf16_cones_equal_dense(case, monkeypatch):
     assert torch.equal(cone, dense)
     again = ctx.local_energy(cfg, None, 'bf16')     # default plan choice
     assert torch.equal(again, cone)
+
+
+ROW_CASES = [
+    ('j1j2_10x10', {}),
+    ('j1j2_10x10', {'sign_rule': True}),
+    ('j1j2_4x4', {'channels': 16, 'n_layers': 3}),
+    ('j1j2_10x10', {'L': 7, 'n_up': 25, 'n_down': 24, 'n_layers': 5}),
+    ('j1j2_10x10', {'L': 12, 'n_up': 72, 'n_down': 72, 'n_layers': 4}),
+    ('j1j2_10x10', {'L': 11, 'n_up': 61, 'n_down': 60, 'n_layers': 3}),
+]
+
+
+@pytest.mark.parametrize('case', ROW_CASES, ids=_ids)
+@pytest.mark.parametrize('give_logpsi', [False, True])
+def test_local_energy_row_form_equals_tap_form(case, give_logpsi, monkeypatch):
+    """The row form (rows = lattice row x configuration, x positions along
+    tensor-memory columns, the three dx taps of a kernel row in one N = 3C
+    MMA) accumulates every output's taps in the tap form's order onto a
+    zeroed accumulator, so its local energies equal the tap form's bitwise,
+    and both stay within the bf16 bar of the oracle."""
+    nqs = lib()
+    from tests.gpu_common import problem_of
+    name, over = case
+    w = WL[name]
+    L = over.get('L', w['L'])
+    plan = nqs.tc_plan(problem_of(w, **over), 'local_energy', 4096)
+    assert plan['row_form'] == 1 and plan['blocks_per_sm'] == 2
+    ctx, params = make_ctx(w, **over)
+    cfg_h = configs_for(w, 37, seed=41, **over)
+    cfg = dev(cfg_h)
+    lp = ctx.logpsi(cfg, 'bf16') if give_logpsi else None
+    rows = ctx.local_energy(cfg, lp, 'bf16')
+    monkeypatch.setenv('NQS_TC_ROWS', '0')
+    tap = ctx.local_energy(cfg, lp, 'bf16')
+    monkeypatch.delenv('NQS_TC_ROWS')
+    torch.cuda.synchronize()
+    assert torch.equal(rows, tap)
+    spec, ham = oracle_of(w, **over)
+    want = eloc.local_energy(params, cfg_h[:8], spec, ham)
+    got = rows[:8].cpu().numpy()
+    assert abs(got[:, 0].mean() - want.real.mean()) / L ** 2 <= 1e-4
 
 
 def test_local_energy_bf16_zero_network():

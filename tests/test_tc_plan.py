@@ -69,10 +69,20 @@ def test_plans_fit_across_lattice_sizes(nqs, L, channels):
 
 
 def test_measured_choices(nqs):
-    # 10x10, 16 channels: two blocks per SM with eight configurations each
+    # 10x10, 16 channels: the row form, two blocks per SM with twelve configurations each (120 of the 128
+    # accumulator rows); the log psi plan keeps the tap form
     p10 = nqs.make_problem('j1j2', 10, n_layers=6, channels=16)
     e = nqs.tc_plan(p10, 'local_energy', 8192, MAX_SMEM, NUM_SMS)
-    assert (e['G'], e['slots'], e['blocks_per_sm'], e['grid']) == (8, 1, 2, 2 * NUM_SMS)
+    assert (e['G'], e['slots'], e['blocks_per_sm'], e['grid'], e['row_form']) == (12, 1, 2, 2 * NUM_SMS, 1)
+    assert e['tmem_cols'] == 256 and e['tiles'] == 1
+    lp = nqs.tc_plan(p10, 'logpsi', 8192, MAX_SMEM, NUM_SMS)
+    assert (lp['blocks_per_sm'], lp['row_form']) == (2, 0)
+    # the row form covers J1-J2 with 16 channels up to 13x13; larger lattices and 32 channels keep the tap form
+    for L, want in ((4, 1), (7, 1), (13, 1), (14, 0), (16, 0)):
+        pl = nqs.tc_plan(nqs.make_problem('j1j2', L, n_up=L * L // 2, n_down=L * L - L * L // 2, n_layers=6,
+                                          channels=16), 'local_energy', 4096, MAX_SMEM, NUM_SMS)
+        assert pl['row_form'] == want, L
+        assert pl['G'] == (min(16, 128 // L) if want else pl['G'])
     # 256 chains: one chain per block, two blocks per SM
     s = nqs.tc_plan(p10, 'sample', 256, MAX_SMEM, NUM_SMS)
     assert (s['G'], s['blocks_per_sm'], s['grid']) == (1, 2, 256)
@@ -93,12 +103,15 @@ def test_measured_choices(nqs):
 
 def test_overrides(nqs, monkeypatch):
     p10 = nqs.make_problem('j1j2', 10, n_layers=6, channels=16)
+    monkeypatch.setenv('NQS_TC_ROWS', '0')               # the tap form for the local energy
+    assert nqs.tc_plan(p10, 'local_energy', 8192, MAX_SMEM, NUM_SMS)['row_form'] == 0
     monkeypatch.setenv('NQS_TC_PLAN', '16,1,1')
     e = nqs.tc_plan(p10, 'local_energy', 8192, MAX_SMEM, NUM_SMS)
     assert (e['G'], e['slots'], e['blocks_per_sm']) == (16, 1, 1)
     monkeypatch.setenv('NQS_TC_PLAN', '40,1,1')          # infeasible: ignored
     assert nqs.tc_plan(p10, 'local_energy', 8192, MAX_SMEM, NUM_SMS)['G'] == 8
     monkeypatch.delenv('NQS_TC_PLAN')
+    monkeypatch.delenv('NQS_TC_ROWS')
     monkeypatch.setenv('NQS_TC_SAMPLE', '2,1,1')
     s = nqs.tc_plan(p10, 'sample', 256, MAX_SMEM, NUM_SMS)
     assert (s['G'], s['blocks_per_sm'], s['grid']) == (2, 1, 128)
