@@ -50,6 +50,11 @@ def parse():
                     help='small sampler-only run for profilers: CHAINS chains, 2 samples each')
     ap.add_argument('--profile-grad', type=int, default=0, metavar='S',
                     help='small O_k-only run for profilers: S uniform random samples')
+    ap.add_argument('--profile-sr', type=int, default=0, metavar='S',
+                    help='small SR-only run for profilers: O and E_loc of S uniform random samples, then --steps '
+                         'solves of 8 CG iterations each')
+    ap.add_argument('--no-extra', action='store_true',
+                    help='skip the other workloads (16x16 SR step, t-J 12x12 E_loc, serving mix) after the main line')
     ap.add_argument('--sr-compare', action='store_true',
                     help='time the CG and the sample-space (Woodbury) SR solves on the same O and E_loc')
     ap.add_argument('--serve-partition', action='store_true',
@@ -57,10 +62,10 @@ def parse():
     return ap.parse_args()
 
 
-def serve_mix(n_req, seed=0, mean_gap_s=0.3, steps=2):
-    """Seeded request mix: J1-J2 at L in {6, 8, 10, 12, 16, 24, 36} with J2 ~ U[0.4, 0.6] and t-J 12 x 12 at
-    hole doping 1/16 .. 1/8; 6-8 conv layers, 16 or 32 channels (16 at L = 36, where 32 does not fit on chip),
-    2,048-8,192 samples (2,048 for L >= 24); Poisson arrivals."""
+def serve_mix(n_req, seed=0, mean_gap_s=0.3, steps=2, lattices=(6, 8, 10, 12, 16, 24, 36)):
+    """Seeded request mix: J1-J2 at L in `lattices` (default {6, 8, 10, 12, 16, 24, 36}) with J2 ~ U[0.4, 0.6]
+    and t-J 12 x 12 at hole doping 1/16 .. 1/8; 6-8 conv layers, 16 or 32 channels (16 at L = 36, where 32 does
+    not fit on chip), 2,048-8,192 samples (2,048 for L >= 24); Poisson arrivals."""
     import numpy as np
     import nqs_synth
     from paper_2204_07816_gb300.serving import Request
@@ -77,7 +82,7 @@ def serve_mix(n_req, seed=0, mean_gap_s=0.3, steps=2):
             kw = dict(model='tj', L=12, n_up=(144 - n_h) // 2, n_down=(144 - n_h) // 2, n_layers=n_layers, channels=ch)
             c_in = 3
         else:
-            L = int(rng.choice([6, 8, 10, 12, 16, 24, 36]))
+            L = int(rng.choice(list(lattices)))
             ch = 16 if L == 36 else int(rng.choice([16, 32]))
             ns = 2048 if L >= 24 else int(rng.choice([2048, 4096, 8192]))
             kw = dict(model='j1j2', L=L, J2=float(rng.uniform(0.4, 0.6)), n_layers=n_layers, channels=ch)
@@ -235,6 +240,231 @@ def profile_stage(args):
                       'precision': args.precision, 'ms': times}))
 
 
+def _problem_of(nqs, w):
+    if w['model'] == 'j1j2':
+        return nqs.make_problem('j1j2', w['L'], J1=w['J1'], J2=w['J2'], n_layers=w['n_layers'], channels=w['channels'])
+    return nqs.make_problem('tj', w['L'], t=w['t'], J=w['J'], n_up=w['n_up'], n_down=w['n_down'],
+                            n_layers=w['n_layers'], channels=w['channels'])
+
+
+def sx_iteration(ctx, O, e, iters=(4, 12)):
+    """Device time of one CG iteration (two passes over O and the P-vector kernels): solves of exactly iters[0]
+    and iters[1] iterations (rtol 0), timed with CUDA events on the context's stream; the difference divided by
+    the iteration difference."""
+    import torch
+    times = []
+    for k in iters:
+        best = None
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = ctx.sr_solve(O, e, eps=1e-4, rtol=0.0, max_iter=k, lr=0.0)
+            e1.record()
+            torch.cuda.synchronize()
+            assert info['iters'] == k, info
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        times.append(best)
+    return (times[1] - times[0]) / (iters[1] - iters[0])
+
+
+def sx_roofline(n_samples, P, iter_ms, peaks):
+    """Roofline entry of the S x products: algorithmic bytes 2 passes x 2 n_samples x P x 8 and FP64 FLOP
+    4 x 2 n_samples x P per CG iteration, against the measured copy bandwidth and the nominal FP64 rate."""
+    bytes_it = 2.0 * 2 * n_samples * P * 8
+    flop_it = 4.0 * 2 * n_samples * P
+    gbs = bytes_it / (iter_ms / 1e3) / 1e9
+    tfs = flop_it / (iter_ms / 1e3) / 1e12
+    return {'kernels': 'gemv_rows_kernel + gemv_cols_kernel (+ P-vector kernels)', 'ms_per_cg_iteration': iter_ms,
+            'bytes_per_iteration': bytes_it, 'flop_per_iteration': flop_it,
+            'hbm': {'achieved': gbs, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s', 'frac': gbs / peaks['hbm_gbs']},
+            'fp64': {'achieved': tfs, 'peak': 1.25, 'unit': 'TFLOP/s', 'frac': tfs / 1.25,
+                     'peak_source': 'nominal FP64 rate of GB300'}}
+
+
+def profile_sr(args):
+    """Small SR-only run for profilers: O and E_loc of S uniform random samples (bf16 path), then --steps solves
+    of exactly 8 CG iterations each."""
+    import torch
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300 import nqs
+    nbuild.build()
+    w = nqs_synth.WORKLOADS[args.workload]
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    ctx = nqs.Context(_problem_of(nqs, w), torch.tensor(params, dtype=torch.float64, device='cuda'), seed=1)
+    cfg = torch.from_numpy(nqs_synth.random_configs(w['L'] ** 2, w['n_up'], w['n_down'], args.profile_sr, 3)).cuda()
+    e = ctx.local_energy(cfg, None, args.precision)
+    O = ctx.logpsi_grad(cfg, args.precision)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.sr_solve(O, e, eps=1e-4, rtol=0.0, max_iter=8, lr=0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.sync()
+    print(json.dumps({'mode': 'profile-sr', 'workload': args.workload, 'samples': args.profile_sr,
+                      'P': ctx.P, 'ms_per_8_iterations': times}))
+
+
+class UtilSampler:
+    """GPU utilisation (the share of time a kernel was running) sampled by nvidia-smi while a region runs."""
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix='.csv')
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '--query-gpu=uuid,utilization.gpu', '--format=csv,noheader,nounits',
+                                          '-lms', '100', '-f', self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        vals = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [q.strip() for q in line.split(',')]
+                if len(parts) == 2 and (not self.uuid or self.uuid in parts[0]) and parts[1].isdigit():
+                    vals.append(float(parts[1]))
+        os.unlink(self.path)
+        return {'mean_pct': statistics.mean(vals), 'samples': len(vals)} if vals else None
+
+
+def extra_workloads(args, peaks, uuid, pool, cores):
+    """The metric's other workloads on the same GPU, after the main line: the 16x16 SR step (32 channels,
+    8 layers, 16,384 samples), t-J 12x12 E_loc (32 channels, 8,192 samples) with its energy checks, and a short
+    serving mix of lattices up to 16x16 (continuous batching; p50/p99, throughput, GPU-busy share)."""
+    import numpy as np
+    import torch
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import nqs
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    def tc_roofline(w, ctx, cfg, eloc_ms):
+        n = cfg.shape[0]
+        n_conn, pairs, _, _ = ctx.connected(cfg)
+        flops, flops_dense = eloc_algorithmic_flops(w, n, pairs, n_conn)
+        peak = peaks.get('bf16_tflops_sustained') or peaks['bf16_tflops']
+        ach = flops / (eloc_ms / 1e3) / 1e12
+        ach_d = flops_dense / (eloc_ms / 1e3) / 1e12
+        return {'bound': 'tensor', 'achieved': ach, 'peak': peak, 'unit': 'TFLOP/s', 'frac': ach / peak,
+                'dense_form': {'achieved': ach_d, 'frac': ach_d / peak},
+                'flops': 'cone form %.4g, dense form %.4g per launch' % (flops, flops_dense)}
+
+    # ---- 16 x 16 J1-J2, 32 channels, 8 layers: one SR step = sample + E_loc + O_k + CG + update
+    w = nqs_synth.WORKLOADS['j1j2_16x16']
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    ctx = nqs.Context(_problem_of(nqs, w), torch.tensor(params, dtype=torch.float64, device='cuda'), seed=11)
+    P = ctx.P
+    spc = w['n_samples'] // w['n_chains']
+    stages = []
+    infos = []
+    for k in range(3):   # one warm-up step (with burn-in), two timed
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        cfg, _ = ctx.sample(w['n_chains'], spc, 1, 10 if k == 0 else 0, 'bf16')
+        ev[1].record(stream)
+        e = ctx.local_energy(cfg, None, 'bf16')
+        ev[2].record(stream)
+        O = ctx.logpsi_grad(cfg, 'bf16')
+        ev[3].record(stream)
+        _, info = ctx.sr_solve(O, e, eps=1e-4, rtol=1e-8, max_iter=min(P, 10000), lr=0.02, apply_update=True)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+            infos.append(info)
+    st = np.array(stages)
+    eloc_ms = float(st[:, 1].mean())
+    it_ms = sx_iteration(ctx, O, e)
+    sub = cfg[:32].contiguous()
+    e64 = ctx.local_energy(sub, None, 'fp64').cpu().numpy()
+    e16 = ctx.local_energy(sub, None, 'bf16').cpu().numpy()
+    out['j1j2_16x16'] = {
+        'workload': 'J1-J2 16x16, 8 conv layers x 32 channels (P = %d), %d samples / %d chains' % (
+            P, w['n_samples'], w['n_chains']),
+        'sr_steps_per_s': 1000.0 / float(st.sum(axis=1).mean()),
+        'stage_ms': {k: float(st[:, i].mean()) for i, k in enumerate(['sample', 'eloc', 'grad', 'sr'])},
+        'cg_iters': [int(i['iters']) for i in infos],
+        'eloc_samples_per_s': w['n_samples'] / (eloc_ms / 1e3),
+        'roofline_eloc': tc_roofline(w, ctx, cfg, eloc_ms),
+        'sx': sx_roofline(w['n_samples'], P, it_ms, peaks),
+        'energy_per_site_vs_fp64_gpu': abs(e16[:, 0].mean() - e64[:, 0].mean()) / w['L'] ** 2,
+        'fp64_check_samples': int(sub.shape[0])}
+    del O
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    # ---- t-J 12 x 12, 32 channels, 6 layers: E_loc of 8,192 sampled configurations
+    w = nqs_synth.WORKLOADS['tj_12x12']
+    params = nqs_synth.random_params(w['c_in'], w['channels'], w['n_layers'], seed=1)
+    ctx = nqs.Context(_problem_of(nqs, w), torch.tensor(params, dtype=torch.float64, device='cuda'), seed=12)
+    cfg, _ = ctx.sample(w['n_chains'], w['n_samples'] // w['n_chains'], 1, 10, 'bf16')
+    ctx.local_energy(cfg, None, 'bf16')
+    times = []
+    for _ in range(3):
+        e, t = timed(lambda: ctx.local_energy(cfg, None, 'bf16'))
+        times.append(t)
+    eloc_ms = float(np.mean(times))
+    sub = cfg[:256].contiguous()
+    e64 = ctx.local_energy(sub, None, 'fp64').cpu().numpy()
+    e16 = e[:256].cpu().numpy()
+    N = w['L'] ** 2
+    osub = cfg[:min(args.oracle_samples, 32)].cpu().numpy()
+    e_or, _ = oracle_eloc('tj_12x12', params, osub, pool, cores)
+    out['tj_12x12'] = {
+        'workload': 't-J 12x12 (t=1, J=0.4, 18 holes), 6 conv layers x 32 channels, %d sampled configurations' %
+                    w['n_samples'],
+        'eloc_samples_per_s': w['n_samples'] / (eloc_ms / 1e3), 'eloc_ms': eloc_ms,
+        'roofline_eloc': tc_roofline(w, ctx, cfg, eloc_ms),
+        'energy_per_site_vs_fp64_gpu': abs(e16[:, 0].mean() - e64[:, 0].mean()) / N,
+        'fp64_check_samples': int(sub.shape[0]),
+        'energy_per_site_vs_oracle_subset': abs(e16[:osub.shape[0], 0].mean() - e_or.real.mean()) / N,
+        'oracle_subset_samples': int(osub.shape[0])}
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    # ---- serving: a seeded mix of lattices up to 16 x 16 arriving faster than they run
+    from paper_2204_07816_gb300.serving import Server
+    reqs = serve_mix(10, seed=3, mean_gap_s=0.02, steps=2, lattices=(6, 8, 10, 12, 16))
+    util = UtilSampler(uuid)
+    util.start()
+    server = Server(device='cuda', precision='bf16')
+    _, summary = server.run(reqs)
+    busy = util.stop()
+    summary['gpu_busy'] = busy
+    summary['mix'] = '10 requests x 2 SR steps: J1-J2 L in {6..16} and t-J 12x12, 16/32 channels, 2,048-8,192 ' \
+                     'samples, Poisson arrivals 20 ms apart on average (seed 3)'
+    out['serving'] = summary
+    return out
+
+
 def dense_forward_flops(w):
     N = w['L'] ** 2
     fl = 0
@@ -288,8 +518,8 @@ def eloc_algorithmic_flops(w, n_samples, pairs, n_conn):
 TRAFFIC_SOURCES = ('tc.cu', 'tc_ptx.cuh', 'common.cuh', 'internal.h')
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one E_loc launch captured by ncu under
 # `bench.py --profile-eloc 2048`, with the hash of the kernel sources it was taken on
-TRAFFIC_RECORD = {'kernel': 'eloc_tc_kernel', 'samples': 2048, 'dram_bytes': 1811456,
-                  'source_sha256': '535bb2c0dbb03e751350b43c4e7c8151a5f913d06ede107b567cdfba83323b8b'}
+TRAFFIC_RECORD = {'kernel': 'eloc_rows_kernel', 'samples': 2048, 'dram_bytes': 737024,
+                  'source_sha256': '3497966dfb7fbce29458c21266c5535d16887eb62b50131371d96cbd04c4ae15'}
 
 
 def kernel_source_hash():
@@ -301,11 +531,11 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(n_samples):
+def recorded_traffic(n_samples, kernel):
     """DRAM bytes (read + write) of one E_loc launch of n_samples, scaled
-    linearly from TRAFFIC_RECORD, or None once the kernel sources differ from
-    the ones the record was taken on."""
-    if TRAFFIC_RECORD['source_sha256'] != kernel_source_hash():
+    linearly from TRAFFIC_RECORD, or None if the record is of another kernel or
+    the kernel sources differ from the ones it was taken on."""
+    if TRAFFIC_RECORD['kernel'] != kernel or TRAFFIC_RECORD['source_sha256'] != kernel_source_hash():
         return None
     return float(TRAFFIC_RECORD['dram_bytes']) * n_samples / float(TRAFFIC_RECORD['samples'])
 
@@ -454,6 +684,9 @@ def main():
         return
     if args.profile_sample or args.profile_grad:
         profile_stage(args)
+        return
+    if args.profile_sr:
+        profile_sr(args)
         return
     if args.serve:
         run_serve(args)
@@ -607,9 +840,12 @@ def main():
         eloc_launch_s = float(eloc_ms.mean()) / 1000.0
         achieved = flops / eloc_launch_s / 1e12
         if args.precision == 'bf16':
+            eloc_kernel = ('eloc_rows_kernel' if nqs.tc_plan(prob, 'local_energy', n_samples)['row_form']
+                           else 'eloc_tc_kernel')
             peak = peaks.get('bf16_tflops_sustained') or peaks['bf16_tflops']
             roof = {'bound': 'tensor', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s',
-                    'frac': achieved / peak, 'traffic': recorded_traffic(n_samples), 'kernel': 'eloc_tc_kernel',
+                    'frac': achieved / peak, 'traffic': recorded_traffic(n_samples, eloc_kernel),
+                    'kernel': eloc_kernel,
                     'peak_source': '%s bf16 dense (sustained)' % peak_kind,
                     'flops': 'cone form (changed sites only) %.4g per launch' % flops,
                     'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,
@@ -632,6 +868,8 @@ def main():
                     'flops': 'cone form (changed sites only) %.4g per launch' % flops,
                     'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,
                                    'frac': flops_dense / eloc_launch_s / 1e12 / peak}}
+        # S x products of the main workload: one CG iteration timed alone
+        sx = sx_roofline(n_samples, P, sx_iteration(ctx, ctx.logpsi_grad(cfg_last, args.precision), e_last), peaks)
         # CPU oracle on a bounded sample of the same workload
         sub = cfg_last[:args.oracle_samples].cpu().numpy()
         e_or, dt_or = oracle_eloc(args.workload, params_at_step(ctx), sub, pool, cores)
@@ -651,6 +889,7 @@ def main():
             'vs_plain_fp32': cmp,
             'energy_check': check,
             'roofline': roof,
+            'roofline_sx': sx,
             'cpu_baseline': {'value': sub.shape[0] / dt_or, 'unit': 'samples/s', 'cores': cores, 'kind': 'oracle',
                              'sample': '%d of the step\'s samples, E_loc only (FP64 numpy oracle, spawn pool)' %
                                        sub.shape[0]},
@@ -660,6 +899,8 @@ def main():
             'gpu_launches': int(launches),
             'clocks': clocks,
         }
+        if not args.no_extra and world == 1:
+            line['extra'] = extra_workloads(args, peaks, uuid, pool, cores)
         print(json.dumps(line), flush=True)
     ctx.close()
     if pool is not None:
