@@ -242,6 +242,19 @@ int nqs_set_chains(nqs_ctx *ctx, int32_t n_chains, const int8_t *chains, uint64_
  * O_k = row s + i * row (n + s). */
 int nqs_logpsi_grad(nqs_ctx *ctx, const int8_t *configs, int64_t n, double *O_out, int32_t precision);
 
+/* Vector-Jacobian product of log psi (the backward of Sec. 3.2 seeded by
+ * the caller): grad_params[k] = sum_s (grad_logpsi[s][0] d a(S_s)/d theta_k
+ * + grad_logpsi[s][1] d phi(S_s)/d theta_k), for n configurations (device
+ * int8 [n][N]) and output gradients grad_logpsi (device float64 [n][2]);
+ * grad_params: device float64 [P]. One backward pass per sample, seeded with
+ * g_a w_a + g_phi w_phi, is summed into per-chunk partials (chunks of
+ * consecutive samples whose size depends on n only, samples in order) that
+ * are added in chunk order, so the result does not depend on the device or
+ * the grid; no [2n][P] matrix is formed. Precisions as nqs_logpsi_grad
+ * (NQS_BF16 differentiates with float32 internals). n = 0 writes zeros. */
+int nqs_logpsi_vjp(nqs_ctx *ctx, const int8_t *configs, int64_t n, const double *grad_logpsi, double *grad_params,
+                   int32_t precision);
+
 /* Local derivatives without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (code that runs where allocating is not allowed, such as an

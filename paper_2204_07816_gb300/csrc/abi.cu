@@ -481,6 +481,37 @@ int nqs_logpsi_grad(nqs_ctx *c, const int8_t *configs, int64_t n, double *O, int
     return launch_grad_plain(c->p, gp, dp, configs, n, O, c->scratch, c->scratch_bytes, env);
 }
 
+int nqs_logpsi_vjp(nqs_ctx *c, const int8_t *configs, int64_t n, const double *grad_logpsi, double *grad_params,
+                   int32_t prec) {
+    NvtxRange nvtx_range("nqs_logpsi_vjp");
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0 || !grad_params || (n > 0 && (!configs || !grad_logpsi)))
+        return fail(c, NQS_ERR_INVALID_ARG, "nqs_logpsi_vjp: bad arrays");
+    if (!valid_precision(prec)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_logpsi_vjp: bad precision");
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(grad_params, 0, sizeof(double) * (size_t)c->p.P, c->stream);
+        return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_logpsi_vjp: clear");
+    }
+    // float32 internals for the tensor-core precision, as nqs_logpsi_grad
+    const int gp = prec == NQS_FP64 ? NQS_FP64 : NQS_FP32;
+    DeviceParams dp;
+    if (int rc = prepare_params(c, gp, &dp)) return rc;
+    const int64_t K = vjp_chunk_samples(n), nq = (n + K - 1) / K;
+    const size_t part_bytes = ((size_t)nq * c->p.P * sizeof(double) + 255) & ~(size_t)255;
+    const bool fast = gp == NQS_FP32 && grad_fast_supported(c->p, c->max_smem);
+    const int blocks = (int)std::min<int64_t>(nq, (int64_t)sms_of(c) * (fast ? grad_fast_blocks_per_sm(c->p) : 2));
+    const size_t work = fast ? grad_fast_scratch_bytes(c->p, blocks) : grad_scratch_bytes(c->p, gp, blocks);
+    if (int rc = ensure_scratch(c, part_bytes + work)) return rc;
+    LaunchEnv env = env_of(c);
+    double *part = (double *)c->scratch;
+    void *ws = (unsigned char *)c->scratch + part_bytes;
+    const size_t ws_bytes = c->scratch_bytes - part_bytes;
+    int rc = fast ? launch_vjp_fast(c->p, c->params32, c->params, configs, n, grad_logpsi, part, ws, ws_bytes, env)
+                  : launch_vjp_plain(c->p, gp, dp, configs, n, grad_logpsi, part, ws, ws_bytes, env);
+    if (rc) return rc;
+    return launch_vjp_reduce(c->p, part, n, grad_params, env);
+}
+
 int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, double eps, double rtol,
                  int32_t max_iter, double lr, double *delta, int32_t *iters_out, double *resid_out,
                  double *energy_out, int32_t apply_update) {

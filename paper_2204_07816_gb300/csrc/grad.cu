@@ -12,6 +12,13 @@
 // Every working array of the current layer lives in shared memory with a
 // site stride of N + 1 (odd) so that threads reading different channels hit
 // different banks; neighbour indices come from a table built once.
+//
+// Vector-Jacobian form (VJP = true): given per-sample output gradients
+// (g_a, g_phi), one backward stream seeded with g_a w_a + g_phi w_phi gives
+// g_a d a / d theta + g_phi d phi / d theta for every parameter, and the
+// samples' vectors are summed per chunk of consecutive samples (each chunk
+// owned by one block, samples in order) into chunk partials; a second kernel
+// sums the partials in chunk order. No per-sample row is stored.
 #include <algorithm>
 
 #include "internal.h"
@@ -48,35 +55,45 @@ __host__ __device__ inline GradLayout grad_layout(const Problem &p) {
     return g;
 }
 
-template <int C>
-__global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_kernel(Problem p, const float *__restrict__ prm,
-                                                                const double *__restrict__ p64,
-                                                                const int8_t *__restrict__ configs, int64_t n,
-                                                                double *__restrict__ O, float *__restrict__ scratch,
-                                                                size_t per_block) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const GradLayout gl = grad_layout(p);
-    const int N = p.N, NP = gl.NP, L = p.L, nl = p.n_layers, P = p.P;
-    float *w = reinterpret_cast<float *>(smem + gl.w);
-    int16_t *nbr = reinterpret_cast<int16_t *>(smem + gl.nbr);      // [9][N]: site at (x + dx, y + dy)
-    float *hprev = reinterpret_cast<float *>(smem + gl.hprev);      // [cin][NP]
-    float *gz = reinterpret_cast<float *>(smem + gl.gz);            // [2][C][NP] (forward: output h)
-    float *gnext = reinterpret_cast<float *>(smem + gl.gnext);      // [2][C][NP]
-    float *hbar = reinterpret_cast<float *>(smem + gl.hbar);
-    float *Hs = scratch + per_block * blockIdx.x;                    // [nl][C][N] h
-    float *Ss = Hs + (size_t)nl * C * N;                             // [nl][C][N] sigmoid(z)
+// The shared-memory working set of one block.
+struct GradSmem {
+    float *w, *hprev, *gz, *gnext, *hbar;
+    int16_t *nbr;
+};
 
+__device__ GradSmem grad_smem(const Problem &p, unsigned char *smem) {
+    const GradLayout gl = grad_layout(p);
+    GradSmem m;
+    m.w = reinterpret_cast<float *>(smem + gl.w);
+    m.nbr = reinterpret_cast<int16_t *>(smem + gl.nbr);      // [9][N]: site at (x + dx, y + dy)
+    m.hprev = reinterpret_cast<float *>(smem + gl.hprev);    // [cin][NP]
+    m.gz = reinterpret_cast<float *>(smem + gl.gz);          // [R][C][NP] (forward: output h)
+    m.gnext = reinterpret_cast<float *>(smem + gl.gnext);    // [R][C][NP]
+    m.hbar = reinterpret_cast<float *>(smem + gl.hbar);
+    const int N = p.N, L = p.L;
     for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
         const int k = e / N, s = e - k * N;
         const int x = s % L, y = s / L, dy = k / 3 - 1, dx = k % 3 - 1;
-        nbr[e] = (int16_t)((((y + dy) % L + L) % L) * L + ((x + dx) % L + L) % L);
+        m.nbr[e] = (int16_t)((((y + dy) % L + L) % L) * L + ((x + dx) % L + L) % L);
     }
     __syncthreads();
+    return m;
+}
 
-    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x) {
-        double *Oa = O + (size_t)smp * P;
-        double *Op = O + (size_t)(n + smp) * P;
-        const int8_t *cfg = configs + smp * N;
+// Backward of one sample. VJP = false: rows Oa = d a / d theta and
+// Op = d phi / d theta are written (two streams). VJP = true: one stream
+// seeded with ga w_a + gp w_phi, and the sample's vector is added to acc
+// (every parameter by the same thread for every sample of the block).
+template <int C, bool VJP>
+__device__ void grad_sample(const Problem &p, const GradSmem &m, const float *__restrict__ prm,
+                            const double *__restrict__ p64, const int8_t *__restrict__ cfg, double *Oa, double *Op,
+                            double ga, double gp, double *acc, float *Hs) {
+    constexpr int R = VJP ? 1 : 2;
+    const int N = p.N, NP = p.N + 1, L = p.L, nl = p.n_layers;
+    float *w = m.w, *hprev = m.hprev, *gz = m.gz, *gnext = m.gnext, *hbar = m.hbar;
+    const int16_t *nbr = m.nbr;
+    float *Ss = Hs + (size_t)nl * C * N;                             // [nl][C][N] sigmoid(z)
+    {
         // ---------------- forward
         for (int s = threadIdx.x; s < N; s += blockDim.x) {
             const int v = cfg[s];
@@ -149,21 +166,27 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
         __syncthreads();
         const int ho = head_offset(p);
         for (int c = threadIdx.x; c < C; c += blockDim.x) {
-            Oa[ho + c] = (double)hbar[c];
-            Oa[ho + C + c] = 0.0;
-            Op[ho + c] = 0.0;
-            Op[ho + C + c] = (double)hbar[c];
+            if (VJP) {
+                acc[ho + c] += ga * (double)hbar[c];
+                acc[ho + C + c] += gp * (double)hbar[c];
+            } else {
+                Oa[ho + c] = (double)hbar[c];
+                Oa[ho + C + c] = 0.0;
+                Op[ho + c] = 0.0;
+                Op[ho + C + c] = (double)hbar[c];
+            }
         }
-        for (int e = threadIdx.x; e < 2 * C * N; e += blockDim.x) {
+        for (int e = threadIdx.x; e < R * C * N; e += blockDim.x) {
             const int r = e / (C * N), rem = e - r * C * N, c = rem / N, s = rem - c * N;
-            gnext[(r * C + c) * NP + s] = (float)p64[ho + r * C + c];
+            gnext[(r * C + c) * NP + s] =
+                VJP ? (float)(ga * p64[ho + c] + gp * p64[ho + C + c]) : (float)p64[ho + r * C + c];
         }
         // ---------------- backward
         for (int l = nl - 1; l >= 0; --l) {
             const int cin = layer_cin(p, l), off = layer_offset(p, l);
             const float *Hl = Hs + (size_t)l * C * N, *Sl = Ss + (size_t)l * C * N;
             __syncthreads();
-            for (int e = threadIdx.x; e < 2 * C * N; e += blockDim.x) {
+            for (int e = threadIdx.x; e < R * C * N; e += blockDim.x) {
                 const int r = e / (C * N), rem = e - r * C * N, c = rem / N, s = rem - c * N;
                 const float h = Hl[c * N + s], sg = Sl[c * N + s];
                 gz[(r * C + c) * NP + s] = gnext[(r * C + c) * NP + s] * (sg + h * (1.0f - sg));
@@ -193,7 +216,7 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
                 float a0[9], a1[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) { a0[k] = 0.f; a1[k] = 0.f; }
-                const float *g0 = gz + o * NP, *g1 = gz + (C + o) * NP;
+                const float *g0 = gz + o * NP, *g1 = gz + ((R - 1) * C + o) * NP;
                 const float *hc = hprev + c * NP;
                 // sites in row-major order with the 3 x 3 input window held in registers: moving one site
                 // along x reuses six of its values and loads the three of the new column
@@ -214,7 +237,7 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
 #pragma unroll
                             for (int dx = 0; dx < 3; ++dx) {
                                 a0[3 * dy + dx] = fmaf(x0, win[dy][dx], a0[3 * dy + dx]);
-                                a1[3 * dy + dx] = fmaf(x1, win[dy][dx], a1[3 * dy + dx]);
+                                if (!VJP) a1[3 * dy + dx] = fmaf(x1, win[dy][dx], a1[3 * dy + dx]);
                             }
                         const int xn = x + 2 < L ? x + 2 : x + 2 - L;
 #pragma unroll
@@ -227,27 +250,34 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
                 }
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
-                    Oa[off + (o * cin + c) * 9 + k] = (double)a0[k];
-                    Op[off + (o * cin + c) * 9 + k] = (double)a1[k];
+                    if (VJP) {
+                        acc[off + (o * cin + c) * 9 + k] += (double)a0[k];
+                    } else {
+                        Oa[off + (o * cin + c) * 9 + k] = (double)a0[k];
+                        Op[off + (o * cin + c) * 9 + k] = (double)a1[k];
+                    }
                 }
             }
             {
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-                for (int ro = warp; ro < 2 * C; ro += nw) {
+                for (int ro = warp; ro < R * C; ro += nw) {
                     float v = 0.f;
                     for (int s = lane; s < N; s += 32) v += gz[ro * NP + s];
 #pragma unroll
                     for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
-                    if (lane == 0) (ro < C ? Oa : Op)[off + 9 * cin * C + (ro % C)] = (double)v;
+                    if (lane == 0) {
+                        if (VJP) acc[off + 9 * cin * C + ro] += (double)v;
+                        else (ro < C ? Oa : Op)[off + 9 * cin * C + (ro % C)] = (double)v;
+                    }
                 }
             }
             if (l > 0) {
                 // input gradient g_{l-1}[r][c][s] = sum_{o,k} W[o][c][k] gz[r][o][s - d_k]
-                for (int rs = threadIdx.x; rs < 2 * N; rs += blockDim.x) {
+                for (int rs = threadIdx.x; rs < R * N; rs += blockDim.x) {
                     const int r = rs / N, s = rs - r * N;
-                    float acc[C];
+                    float ac[C];
 #pragma unroll
-                    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+                    for (int c = 0; c < C; ++c) ac[c] = 0.f;
                     const float *gr = gz + r * C * NP;
                     for (int k = 0; k < 9; ++k) {
                         const int sm = nbr[(8 - k) * N + s];   // site - d_k
@@ -257,15 +287,15 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
 #pragma unroll
                             for (int q = 0; q < C / 4; ++q) {
                                 const float4 wv = wr[q];
-                                acc[4 * q] = fmaf(wv.x, gv, acc[4 * q]);
-                                acc[4 * q + 1] = fmaf(wv.y, gv, acc[4 * q + 1]);
-                                acc[4 * q + 2] = fmaf(wv.z, gv, acc[4 * q + 2]);
-                                acc[4 * q + 3] = fmaf(wv.w, gv, acc[4 * q + 3]);
+                                ac[4 * q] = fmaf(wv.x, gv, ac[4 * q]);
+                                ac[4 * q + 1] = fmaf(wv.y, gv, ac[4 * q + 1]);
+                                ac[4 * q + 2] = fmaf(wv.z, gv, ac[4 * q + 2]);
+                                ac[4 * q + 3] = fmaf(wv.w, gv, ac[4 * q + 3]);
                             }
                         }
                     }
 #pragma unroll
-                    for (int c = 0; c < C; ++c) gnext[(r * C + c) * NP + s] = acc[c];
+                    for (int c = 0; c < C; ++c) gnext[(r * C + c) * NP + s] = ac[c];
                 }
             }
         }
@@ -273,7 +303,94 @@ __global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_ker
     }
 }
 
+template <int C>
+__global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) grad_fast_kernel(Problem p, const float *__restrict__ prm,
+                                                                const double *__restrict__ p64,
+                                                                const int8_t *__restrict__ configs, int64_t n,
+                                                                double *__restrict__ O, float *__restrict__ scratch,
+                                                                size_t per_block) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GradSmem m = grad_smem(p, smem);
+    float *Hs = scratch + per_block * blockIdx.x;                    // [nl][C][N] h, then sigmoid(z)
+    for (int64_t smp = blockIdx.x; smp < n; smp += gridDim.x)
+        grad_sample<C, false>(p, m, prm, p64, configs + smp * p.N, O + (size_t)smp * p.P, O + (size_t)(n + smp) * p.P,
+                              0.0, 0.0, nullptr, Hs);
+}
+
+// Vector-Jacobian products summed per chunk: chunk q holds samples
+// [q K, min(n, (q + 1) K)) and its partial row part[q][P] is owned by one
+// block; grad[n][2] = (g_a, g_phi) per sample.
+template <int C>
+__global__ void __launch_bounds__(kGradThreads, kGradMinBlocks<C>) vjp_fast_kernel(Problem p, const float *__restrict__ prm,
+                                                               const double *__restrict__ p64,
+                                                               const int8_t *__restrict__ configs, int64_t n,
+                                                               const double *__restrict__ grad, int64_t K,
+                                                               double *__restrict__ part, float *__restrict__ scratch,
+                                                               size_t per_block) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GradSmem m = grad_smem(p, smem);
+    float *Hs = scratch + per_block * blockIdx.x;
+    const int64_t nq = (n + K - 1) / K;
+    for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        double *acc = part + (size_t)q * p.P;
+        for (int k = threadIdx.x; k < p.P; k += blockDim.x) acc[k] = 0.0;
+        __syncthreads();
+        const int64_t s1 = min(n, (q + 1) * K);
+        for (int64_t smp = q * K; smp < s1; ++smp)
+            grad_sample<C, true>(p, m, prm, p64, configs + smp * p.N, nullptr, nullptr, grad[2 * smp],
+                                 grad[2 * smp + 1], acc, Hs);
+    }
+}
+
+// out[k] = sum over chunks q = 0 .. nq - 1 (in order) of part[q][k].
+__global__ void vjp_reduce_kernel(const double *__restrict__ part, int64_t nq, int P, double *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    double v = 0.0;
+    for (int64_t q = 0; q < nq; ++q) v += part[(size_t)q * P + k];
+    out[k] = v;
+}
+
 }  // namespace
+
+int64_t vjp_chunk_samples(int64_t n) { return std::max<int64_t>(1, (n + 1023) / 1024); }
+
+int launch_vjp_reduce(const Problem &p, const double *part, int64_t n, double *out, const LaunchEnv &env) {
+    const int64_t nq = (n + vjp_chunk_samples(n) - 1) / vjp_chunk_samples(n);
+    vjp_reduce_kernel<<<(p.P + 255) / 256, 256, 0, env.stream>>>(part, nq, p.P, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *env.msg = std::string("vjp_reduce_kernel: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    ++*env.launches;
+    return NQS_OK;
+}
+
+int launch_vjp_fast(const Problem &p, const float *p32, const double *p64, const int8_t *configs, int64_t n,
+                    const double *grad, double *part, void *scratch, size_t scratch_bytes, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    const GradLayout gl = grad_layout(p);
+    const size_t per_block = (size_t)2 * p.n_layers * p.C * p.N;   // floats
+    const int64_t K = vjp_chunk_samples(n), nq = (n + K - 1) / K;
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(nq, (int64_t)env.num_sms * grad_fast_blocks_per_sm(p)),
+                             (int64_t)(scratch_bytes / (per_block * sizeof(float)))));
+    if (int rc = allow_dynamic_smem(p.C == 16 ? vjp_fast_kernel<16> : vjp_fast_kernel<32>, gl.total, env)) return rc;
+    if (p.C == 16)
+        vjp_fast_kernel<16><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, grad, K, part,
+                                                                            (float *)scratch, per_block);
+    else
+        vjp_fast_kernel<32><<<blocks, kGradThreads, gl.total, env.stream>>>(p, p32, p64, configs, n, grad, K, part,
+                                                                            (float *)scratch, per_block);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *env.msg = std::string("vjp_fast_kernel: ") + cudaGetErrorString(e);
+        return NQS_ERR_CUDA;
+    }
+    ++*env.launches;
+    return NQS_OK;
+}
 
 int grad_fast_blocks_per_sm(const Problem &p) {
     const size_t smem = grad_layout(p).total + 1024;

@@ -74,6 +74,15 @@ size_t grad_fast_scratch_bytes(const Problem &p, int num_blocks);
 int launch_grad_fast(const Problem &p, const float *p32, const double *p64, const int8_t *configs, int64_t n,
                      double *O, void *scratch, size_t scratch_bytes, const LaunchEnv &env);
 void launch_convert_params(const double *p64, float *p32, int P, cudaStream_t s);
+// vector-Jacobian products sum_s (g_a d a_s / d theta + g_phi d phi_s / d theta): per-chunk partials
+// part[ceil(n / K)][P] (K = vjp_chunk_samples(n), one block per chunk, samples in order), then
+// launch_vjp_reduce sums the chunks in order
+int64_t vjp_chunk_samples(int64_t n);
+int launch_vjp_fast(const Problem &p, const float *p32, const double *p64, const int8_t *configs, int64_t n,
+                    const double *grad, double *part, void *scratch, size_t scratch_bytes, const LaunchEnv &env);
+int launch_vjp_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
+                     const double *grad, double *part, void *scratch, size_t scratch_bytes, const LaunchEnv &env);
+int launch_vjp_reduce(const Problem &p, const double *part, int64_t n, double *out, const LaunchEnv &env);
 
 // ---- tensor-core path (tc.cu)
 bool tc_supported(const Problem &p, std::string *why);
@@ -99,8 +108,9 @@ int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, i
 int launch_wait_probe(int64_t iterations, const LaunchEnv &env);
 int launch_bounds_probe(const LaunchEnv &env);
 // Tensor-core plan the launchers choose (host only): kind 0 log psi, 1 local
-// energy, 2 sampler (n = chains). out[8]: G, slots, blocks per SM, epilogue
-// warps, tiles per group, shared bytes per block, TMEM columns, grid.
+// energy, 2 sampler (n = chains). out[9]: G, slots, blocks per SM, epilogue
+// warps, tiles per group, shared bytes per block, TMEM columns, grid, form
+// (0 tap form, 1 row form).
 int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int num_sms, int32_t *out,
                      std::string *why);
 int launch_sample_tc(const Problem &p, const double *p64, const void *packed, int8_t *chains, int n_chains,

@@ -329,22 +329,24 @@ template <typename T>
 __device__ __forceinline__ T sigmoid_t(T z) { return T(1) / (T(1) + exp(-z)); }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) grad_plain_kernel(Problem p, const T *params, const double *p64,
-                                                              const int8_t *configs, int64_t n, double *O,
-                                                              T *scratch, size_t per_block) {
-    const int N = p.N, C = p.C, L = p.L, nl = p.n_layers, P = p.P;
-    T *base = scratch + per_block * blockIdx.x;
+__device__ __forceinline__ void acc_out(double *acc, int k, T v) { acc[k] += (double)v; }
+
+// One sample. VJP = false: rows Oa, Op of O (two output-gradient streams).
+// VJP = true: one stream seeded with ga w_a + gp w_phi, the sample's vector
+// added to acc (each parameter by the same thread for every sample).
+template <typename T, bool VJP>
+__device__ void grad_plain_sample(const Problem &p, const T *params, const double *p64, const int8_t *cfg, double *Oa,
+                                  double *Op, double ga, double gp, double *acc, T *base, T *hbar) {
+    constexpr int R = VJP ? 1 : 2;
+    const int N = p.N, C = p.C, L = p.L, nl = p.n_layers;
     T *h0 = base;                                  // [c_in][N]
     T *z = h0 + (size_t)p.c_in * N;                // [nl][C][N]
     T *h = z + (size_t)nl * C * N;                 // [nl][C][N]
-    T *g = h + (size_t)nl * C * N;                 // [2][C][N]
-    T *gz = g + (size_t)2 * C * N;                 // [2][C][N]
-    __shared__ T hbar[64];
-    for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
-        double *Oa = O + (size_t)s * P;
-        double *Op = O + (size_t)(n + s) * P;
+    T *g = h + (size_t)nl * C * N;                 // [R][C][N]
+    T *gz = g + (size_t)2 * C * N;                 // [R][C][N]
+    {
         for (int r = threadIdx.x; r < N; r += blockDim.x) {
-            const int v = configs[s * N + r];
+            const int v = cfg[r];
             if (p.c_in == 1) h0[r] = (T)v;
             else { h0[r] = (T)(v == 0); h0[N + r] = (T)(v == 1); h0[2 * N + r] = (T)(v == -1); }
         }
@@ -374,22 +376,31 @@ __global__ void __launch_bounds__(kThreads) grad_plain_kernel(Problem p, const T
         __syncthreads();
         const int ho = head_offset(p);
         for (int c = threadIdx.x; c < C; c += blockDim.x) {
-            Oa[ho + c] = (double)hbar[c];
-            Oa[ho + C + c] = 0.0;
-            Op[ho + c] = 0.0;
-            Op[ho + C + c] = (double)hbar[c];
+            if (VJP) {
+                acc[ho + c] += ga * (double)hbar[c];
+                acc[ho + C + c] += gp * (double)hbar[c];
+            } else {
+                Oa[ho + c] = (double)hbar[c];
+                Oa[ho + C + c] = 0.0;
+                Op[ho + c] = 0.0;
+                Op[ho + C + c] = (double)hbar[c];
+            }
         }
         for (int r = threadIdx.x; r < C * N; r += blockDim.x) {
             const int c = r / N;
-            g[r] = (T)p64[ho + c];
-            g[C * N + r] = (T)p64[ho + C + c];
+            if (VJP) {
+                g[r] = (T)(ga * p64[ho + c] + gp * p64[ho + C + c]);
+            } else {
+                g[r] = (T)p64[ho + c];
+                g[C * N + r] = (T)p64[ho + C + c];
+            }
         }
         __syncthreads();
         for (int l = nl - 1; l >= 0; --l) {
             const int cin = layer_cin(p, l), off = layer_offset(p, l);
             const T *zl = z + (size_t)l * C * N;
             const T *hin = l == 0 ? h0 : h + (size_t)(l - 1) * C * N;
-            for (int r = threadIdx.x; r < 2 * C * N; r += blockDim.x) {
+            for (int r = threadIdx.x; r < R * C * N; r += blockDim.x) {
                 const T zz = zl[r % (C * N)];
                 const T sg = sigmoid_t<T>(zz);
                 gz[r] = g[r] * (sg * (T(1) + zz * (T(1) - sg)));
@@ -397,40 +408,73 @@ __global__ void __launch_bounds__(kThreads) grad_plain_kernel(Problem p, const T
             __syncthreads();
             // weight and bias gradients for both outputs
             const int nw = 9 * cin * C;
-            for (int e = threadIdx.x; e < 2 * (nw + C); e += blockDim.x) {
+            for (int e = threadIdx.x; e < R * (nw + C); e += blockDim.x) {
                 const int rr = e / (nw + C), idx = e - rr * (nw + C);
                 const T *gzr = gz + (size_t)rr * C * N;
-                T acc = 0;
+                T a = 0;
                 if (idx < nw) {
                     const int co = idx / (9 * cin), rem = idx - co * 9 * cin, c = rem / 9, o = rem - c * 9;
                     const int dy = o / 3 - 1, dx = o % 3 - 1;
                     for (int site = 0; site < N; ++site) {
                         const int x = site % L, y = site / L;
-                        acc = fma(gzr[co * N + site], hin[c * N + site_at(x + dx, y + dy, L)], acc);
+                        a = fma(gzr[co * N + site], hin[c * N + site_at(x + dx, y + dy, L)], a);
                     }
                 } else {
                     const int co = idx - nw;
-                    for (int site = 0; site < N; ++site) acc += gzr[co * N + site];
+                    for (int site = 0; site < N; ++site) a += gzr[co * N + site];
                 }
-                (rr == 0 ? Oa : Op)[off + idx] = (double)acc;
+                if (VJP) acc_out(acc, off + idx, a);
+                else (rr == 0 ? Oa : Op)[off + idx] = (double)a;
             }
             if (l > 0) {
                 // gradient wrt the layer input: g[c][y][x] = sum_{o, d} W[o][c][d] gz[o][y - dy][x - dx]
-                for (int r = threadIdx.x; r < 2 * C * N; r += blockDim.x) {
+                for (int r = threadIdx.x; r < R * C * N; r += blockDim.x) {
                     const int rr = r / (C * N), rem = r - rr * C * N, c = rem / N, site = rem - c * N;
                     const int x = site % L, y = site / L;
                     const T *gzr = gz + (size_t)rr * C * N;
-                    T acc = 0;
+                    T a = 0;
                     for (int co = 0; co < C; ++co)
                         for (int ky = 0; ky < 3; ++ky)
                             for (int kx = 0; kx < 3; ++kx)
-                                acc = fma(params[off + (co * cin + c) * 9 + ky * 3 + kx],
-                                          gzr[co * N + site_at(x - (kx - 1), y - (ky - 1), L)], acc);
-                    g[r] = acc;
+                                a = fma(params[off + (co * cin + c) * 9 + ky * 3 + kx],
+                                        gzr[co * N + site_at(x - (kx - 1), y - (ky - 1), L)], a);
+                    g[r] = a;
                 }
             }
             __syncthreads();
         }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) grad_plain_kernel(Problem p, const T *params, const double *p64,
+                                                              const int8_t *configs, int64_t n, double *O,
+                                                              T *scratch, size_t per_block) {
+    __shared__ T hbar[64];
+    T *base = scratch + per_block * blockIdx.x;
+    for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
+        grad_plain_sample<T, false>(p, params, p64, configs + s * p.N, O + (size_t)s * p.P, O + (size_t)(n + s) * p.P,
+                                    0.0, 0.0, nullptr, base, hbar);
+}
+
+// Vector-Jacobian products summed per chunk of K consecutive samples (one
+// block per chunk, samples in order) into part[chunk][P].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) vjp_plain_kernel(Problem p, const T *params, const double *p64,
+                                                             const int8_t *configs, int64_t n, const double *grad,
+                                                             int64_t K, double *part, T *scratch, size_t per_block) {
+    __shared__ T hbar[64];
+    T *base = scratch + per_block * blockIdx.x;
+    const int64_t nq = (n + K - 1) / K;
+    for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        double *acc = part + (size_t)q * p.P;
+        for (int k = threadIdx.x; k < p.P; k += blockDim.x) acc[k] = 0.0;
+        __syncthreads();
+        const int64_t s1 = min(n, (q + 1) * K);
+        for (int64_t s = q * K; s < s1; ++s)
+            grad_plain_sample<T, true>(p, params, p64, configs + s * p.N, nullptr, nullptr, grad[2 * s],
+                                       grad[2 * s + 1], acc, base, hbar);
+        __syncthreads();
     }
 }
 
@@ -583,6 +627,23 @@ static size_t grad_per_block(const Problem &p) {
 
 size_t grad_scratch_bytes(const Problem &p, int prec, int num_blocks) {
     return grad_per_block(p) * num_blocks * (prec == NQS_FP64 ? 8 : 4);
+}
+
+int launch_vjp_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,
+                     const double *grad, double *part, void *scratch, size_t scratch_bytes, const LaunchEnv &env) {
+    if (n == 0) return NQS_OK;
+    const size_t esz = prec == NQS_FP64 ? 8 : 4;
+    const int64_t K = vjp_chunk_samples(n), nq = (n + K - 1) / K;
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(nq, (int64_t)env.num_sms * 2),
+                             (int64_t)(scratch_bytes / (grad_per_block(p) * esz))));
+    if (prec == NQS_FP64)
+        vjp_plain_kernel<double><<<blocks, kThreads, 0, env.stream>>>(p, dp.p64, dp.p64, configs, n, grad, K, part,
+                                                                      (double *)scratch, grad_per_block(p));
+    else
+        vjp_plain_kernel<float><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, grad, K, part,
+                                                                     (float *)scratch, grad_per_block(p));
+    return check_launch(env, "vjp_plain_kernel");
 }
 
 int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const int8_t *configs, int64_t n,

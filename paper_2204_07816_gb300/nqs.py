@@ -26,7 +26,7 @@ MODEL = {'j1j2': 0, 'tj': 1}
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
-           'nqs_logpsi_grad', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve',
+           'nqs_logpsi_grad', 'nqs_logpsi_vjp', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve',
            'nqs_sr_solve_woodbury', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_probe_bounds', 'nqs_set_sm_limit',
            'nqs_sampler_counts')
 
@@ -79,6 +79,7 @@ def load(path=None):
         'nqs_get_chains': (ctypes.c_int, [P, I32, P, ctypes.POINTER(U64)]),
         'nqs_set_chains': (ctypes.c_int, [P, I32, P, U64]),
         'nqs_logpsi_grad': (ctypes.c_int, [P, P, I64, P, I32]),
+        'nqs_logpsi_vjp': (ctypes.c_int, [P, P, I64, P, P, I32]),
         'nqs_logpsi_grad_noalloc': (ctypes.c_int, [ctypes.POINTER(nqs_problem), P, P, I64, P, I32, P]),
         'nqs_noalloc_last_error': (ctypes.c_char_p, []),
         'nqs_sr_solve': (ctypes.c_int, [P, P, P, I64, D, D, I32, D, P, ctypes.POINTER(I32), ctypes.POINTER(D),
@@ -319,6 +320,18 @@ class Context:
             out = torch.empty((2 * n, self.P), dtype=torch.float64, device=self.device)
         self._check(self.lib.nqs_logpsi_grad(self.ctx, self._configs(configs), n, _ptr(out, torch.float64, 'O_out'),
                                              _prec(precision)))
+        return out
+
+    def logpsi_vjp(self, configs, grad_logpsi, precision='fp64', out=None):
+        """nqs_logpsi_vjp: sum over samples of g_a d a / d theta + g_phi d phi / d theta ([P] float64)."""
+        n = configs.shape[0]
+        if tuple(grad_logpsi.shape) != (n, 2):
+            raise ValueError('grad_logpsi must be [n, 2]')
+        if out is None:
+            out = torch.empty(self.P, dtype=torch.float64, device=self.device)
+        self._check(self.lib.nqs_logpsi_vjp(self.ctx, self._configs(configs), n,
+                                            _ptr(grad_logpsi, torch.float64, 'grad_logpsi'),
+                                            _ptr(out, torch.float64, 'grad_params'), _prec(precision)))
         return out
 
     def sr_solve_woodbury(self, O, eloc, eps=1e-4, lr=0.02, apply_update=False, delta=None, refine_steps=0):
