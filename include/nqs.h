@@ -67,6 +67,31 @@ typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_BF16 = 2 } nqs_precision;
 
 typedef enum { NQS_MODEL_J1J2 = 0, NQS_MODEL_TJ = 1 } nqs_model;
 
+/* Network family. NQS_NET_SILU: the SiLU convolution stack described at the
+ * top of this file (every precision). NQS_NET_CNN1 / NQS_NET_CNN2: the
+ * paper's two families (Sec. 5.2, "Neural network innovations"), in the
+ * reading below; NQS_FP64 and NQS_FP32 only (NQS_BF16 returns
+ * NQS_ERR_UNSUPPORTED).
+ *   CNN1 (n_layers building blocks; N must be even): U = periodic 3x3
+ *     convolution (cross-correlation) + beta; 1-D max-pooling of window 2,
+ *     stride 2 over the row-major site order; transposed 1-D convolution of
+ *     kernel 2, stride 2 + gamma. Input channels as the SiLU family. The last
+ *     block's transposed convolution has one output channel.
+ *   CNN2: an embedding E[state][C] of the site values (J1-J2: down 0, up 1;
+ *     t-J: hole 0, up 1, down 2), then n_layers blocks of periodic 3x3
+ *     convolution + beta, 1-D max-pooling of window 2, stride 1 (the first
+ *     site copied to the end), transposed 1-D convolution of kernel 2,
+ *     stride 1 (periodic) + gamma; a final periodic 3x3 convolution to one
+ *     channel + beta_f.
+ *   Both: W(S) = product of the N output neurons z_s, so a = sum log|z_s|
+ *   and phi = pi (number of negative z_s mod 2); max-pooling ties go to the
+ *   window's first element; local derivatives are real (d phi = 0).
+ *   Parameter layout: CNN1 per block W[C][C_b][3][3], beta[C], T[C][C_o][2],
+ *   gamma[C_o] (C_b = c_in for the first block, else C; C_o = 1 for the last,
+ *   else C); CNN2 E[n_states][C], per block W[C][C][3][3], beta[C],
+ *   T[C][C][2], gamma[C], then W_f[1][C][3][3], beta_f[1]. */
+typedef enum { NQS_NET_SILU = 0, NQS_NET_CNN1 = 1, NQS_NET_CNN2 = 2 } nqs_net;
+
 /* The physical problem and the network shape. Eq. 2 uses J1, J2 and
  * sign_rule; Eq. 3 uses t and J. n_up / n_down fix the sector the sampler
  * draws from (J1-J2: n_up + n_down = N; t-J: holes = N - n_up - n_down).
@@ -80,8 +105,9 @@ typedef struct {
     double t, J;        /* t-J couplings */
     int32_t n_up, n_down;
     int32_t sign_rule;
-    int32_t n_layers;   /* >= 1 */
+    int32_t n_layers;   /* >= 1 (CNN1 / CNN2: building blocks) */
     int32_t channels;   /* 4, 8, 16 or 32 */
+    int32_t net;        /* nqs_net */
 } nqs_problem;
 
 /* Number of network parameters for problem p (layout above); -1 if p is

@@ -35,6 +35,47 @@ def random_params(c_in, channels, n_layers, seed, scale=0.5):
     return np.concatenate(parts).astype(np.float64)
 
 
+def paper_param_count(kind, c_in, channels, n_blocks):
+    """Parameter count of the paper's CNN1 ('cnn1') / CNN2 ('cnn2') families in the flat layout
+    CNN1: per block W[C][C_b][3][3], beta[C], T[C][C_o][2], gamma[C_o] (C_b = c_in first, C_o = 1 last);
+    CNN2: E[n_states][C]; per block W[C][C][3][3], beta[C], T[C][C][2], gamma[C]; W_f[1][C][3][3], beta_f[1]."""
+    C = channels
+    if kind == 'cnn1':
+        return sum(9 * C * (c_in if b == 0 else C) + C + 2 * C * (1 if b == n_blocks - 1 else C) +
+                   (1 if b == n_blocks - 1 else C) for b in range(n_blocks))
+    ns = 2 if c_in == 1 else 3
+    return ns * C + n_blocks * (11 * C * C + 2 * C) + 9 * C + 1
+
+
+def random_paper_params(kind, c_in, channels, n_blocks, seed, scale=0.5):
+    """Parameters of CNN1 / CNN2 in their flat layout: every tensor N(0, (scale / sqrt(fan_in))^2) with fan_in
+    = 9 C_in (convolutions), C_in (transposed convolutions, kernel 2: one input per output and channel for
+    stride 2) or 1 (embedding); the bias of the one-channel output layer is shifted by +1 so that the neurons
+    whose product is the amplitude start near 1."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    C = channels
+    parts = []
+
+    def draw(n, fan_in, shift=0.0):
+        parts.append(shift + rng.standard_normal(n) * (scale / np.sqrt(float(fan_in))))
+
+    if kind == 'cnn2':
+        draw((2 if c_in == 1 else 3) * C, 1)
+    for b in range(n_blocks):
+        cb = (c_in if b == 0 else C) if kind == 'cnn1' else C
+        co = (1 if b == n_blocks - 1 else C) if kind == 'cnn1' else C
+        draw(9 * C * cb, 9 * cb)
+        draw(C, 9 * cb)
+        draw(2 * C * co, C)
+        draw(co, C, 1.0 if (kind == 'cnn1' and b == n_blocks - 1) else 0.0)
+    if kind == 'cnn2':
+        draw(9 * C, 9 * C)
+        draw(1, 9 * C, 1.0)
+    out = np.concatenate(parts).astype(np.float64)
+    assert out.size == paper_param_count(kind, c_in, channels, n_blocks)
+    return out
+
+
 def random_configs(N, n_up, n_down, count, seed):
     """[count, N] int8, uniform over configurations with n_up (+1), n_down (-1)
     and N - n_up - n_down holes (0)."""

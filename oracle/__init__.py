@@ -18,6 +18,8 @@ Modules
 lattice      sites, bonds and the snake ordering used for fermion signs
 hamiltonian  connected configurations and matrix elements (J1-J2, t-J)
 cnn          the convolutional log-amplitude network, forward and backward
+cnn_paper    the paper's CNN1 / CNN2 families (max-pooling, transposed
+             convolutions, product of neurons), forward and backward
 eloc         local energies
 philox       Philox4x64-10 counter-based generator (Salmon et al., SC'11)
 sampler      Metropolis exchange sampler

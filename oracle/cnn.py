@@ -37,6 +37,8 @@ def layer_dims(spec):
 
 
 def param_count(spec):
+    if _paper(spec):
+        return _paper(spec).param_count(spec)
     return sum(9 * ci * co + co for ci, co in layer_dims(spec)) + 2 * spec.channels
 
 
@@ -90,7 +92,17 @@ def silu_grad(z):
     return s * (1.0 + z * (1.0 - s))
 
 
+def _paper(spec):
+    """The paper's CNN1 / CNN2 families live in cnn_paper (spec.kind)."""
+    if getattr(spec, 'kind', None) in ('cnn1', 'cnn2'):
+        from . import cnn_paper
+        return cnn_paper
+    return None
+
+
 def forward(params, configs, spec, return_cache=False):
+    if _paper(spec):
+        return _paper(spec).forward(params, configs, spec, return_cache)
     layers, w_a, w_phi = unpack(params, spec)
     h = encode(configs, spec)
     cache = [h]
@@ -138,6 +150,8 @@ def backward(params, configs, spec):
     dPhi[b, k] = d phi(S_b) / d theta_k, so that the complex local derivative
     of the paper (O_loc, Sec. 3.2) is O_k = dA + i dPhi.
     """
+    if _paper(spec):
+        return _paper(spec).backward(params, configs, spec)
     layers, w_a, w_phi = unpack(params, spec)
     a, phi, (cache, zs, hbar) = forward(params, configs, spec, return_cache=True)
     B, C = hbar.shape

@@ -10,6 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
+#include "paper_net.cuh"
 
 using namespace nqs;
 
@@ -80,6 +81,11 @@ bool valid_problem(const nqs_problem *q, std::string *why) {
     if (q->model == NQS_MODEL_J1J2 && q->n_up + q->n_down != N) { *why = "J1-J2 needs n_up + n_down = L*L"; return false; }
     if (q->sign_rule != 0 && q->sign_rule != 1) { *why = "sign_rule must be 0 or 1"; return false; }
     if (q->sign_rule && q->model != NQS_MODEL_J1J2) { *why = "sign_rule applies to J1-J2 only"; return false; }
+    if (q->net != NQS_NET_SILU && q->net != NQS_NET_CNN1 && q->net != NQS_NET_CNN2) {
+        *why = "net must be 0 (SiLU stack), 1 (CNN1) or 2 (CNN2)";
+        return false;
+    }
+    if (q->net == NQS_NET_CNN1 && N % 2) { *why = "CNN1 pools pairs of sites: L * L must be even"; return false; }
     return true;
 }
 
@@ -93,7 +99,9 @@ Problem make_problem(const nqs_problem *q) {
     p.n_layers = q->n_layers;
     p.J1 = q->J1; p.J2 = q->J2; p.t = q->t; p.J = q->J;
     p.sign_rule = q->sign_rule;
-    p.P = (9 * p.c_in * p.C + p.C) + (p.n_layers - 1) * (9 * p.C * p.C + p.C) + 2 * p.C;
+    p.net = q->net;
+    p.P = p.net == NQS_NET_SILU ? (9 * p.c_in * p.C + p.C) + (p.n_layers - 1) * (9 * p.C * p.C + p.C) + 2 * p.C
+                                : paper_param_count(p);
     p.n_bonds = (q->model == NQS_MODEL_J1J2 ? 4 : 2) * p.N;
     p.n_up = q->n_up;
     p.n_down = q->n_down;

@@ -32,6 +32,7 @@ struct Problem {
     int P;          // parameter count
     int n_bonds;    // 4N (J1-J2) or 2N (t-J)
     int n_up, n_down;
+    int net;        // NQS_NET_SILU, NQS_NET_CNN1, NQS_NET_CNN2
 };
 
 // Offset of layer l's weights in the flat parameter vector; its bias

@@ -398,7 +398,7 @@ int grad_fast_blocks_per_sm(const Problem &p) {
 }
 
 bool grad_fast_supported(const Problem &p, size_t max_smem) {
-    return (p.C == 16 || p.C == 32) && grad_layout(p).total <= max_smem;
+    return p.net == NQS_NET_SILU && (p.C == 16 || p.C == 32) && grad_layout(p).total <= max_smem;
 }
 
 size_t grad_fast_scratch_bytes(const Problem &p, int num_blocks) {

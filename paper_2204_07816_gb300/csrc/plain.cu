@@ -337,6 +337,10 @@ __device__ __forceinline__ void acc_out(double *acc, int k, T v) { acc[k] += (do
 template <typename T, bool VJP>
 __device__ void grad_plain_sample(const Problem &p, const T *params, const double *p64, const int8_t *cfg, double *Oa,
                                   double *Op, double ga, double gp, double *acc, T *base, T *hbar) {
+    if (p.net != NQS_NET_SILU) {   // the paper's CNN1 / CNN2 (d phi = 0)
+        paper_grad_sample<T, VJP>(p, params, cfg, Oa, Op, ga, acc, base);
+        return;
+    }
     constexpr int R = VJP ? 1 : 2;
     const int N = p.N, C = p.C, L = p.L, nl = p.n_layers;
     T *h0 = base;                                  // [c_in][N]
@@ -622,6 +626,7 @@ int launch_sample_plain(const Problem &p, int prec, const DeviceParams &dp, int8
 }
 
 static size_t grad_per_block(const Problem &p) {
+    if (p.net != NQS_NET_SILU) return paper_grad_per_block(p);
     return (size_t)p.c_in * p.N + 2 * (size_t)p.n_layers * p.C * p.N + 4 * (size_t)p.C * p.N;
 }
 
@@ -732,6 +737,7 @@ extern "C" int nqs_logpsi_grad_noalloc(const nqs_problem *q, const double *param
     p.n_bonds = (q->model == NQS_MODEL_J1J2 ? 4 : 2) * p.N;
     p.n_up = q->n_up;
     p.n_down = q->n_down;
+    p.net = q->net;
     // the bf16 precision differentiates with float32 internals, as nqs_logpsi_grad does; like it, float32 runs
     // grad_fast_kernel (shared-memory working sets, per-block float32 scratch) where that kernel supports the
     // problem, else the plain float kernel

@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "paper_net.cuh"
 
 namespace nqs {
 
@@ -57,6 +58,10 @@ struct PlainNet {
 template <typename T, int CB>
 __device__ void plain_forward(const Problem &p, const T *__restrict__ params, const double *__restrict__ params64,
                               const int8_t *spins, int G, PlainNet<T> &net) {
+    if (p.net != NQS_NET_SILU) {   // the paper's CNN1 / CNN2
+        paper_forward<T>(p, params, spins, G, net.act0, net.act1, net.a, net.phi);
+        return;
+    }
     const int N = p.N, L = p.L, C = p.C;
     // input encoding: J1-J2 one channel (+-1), t-J one-hot (hole, up, down)
     for (int r = threadIdx.x; r < G * N; r += blockDim.x) {

@@ -1717,6 +1717,7 @@ int prep(K kernel, const TcPlan &pl, const LaunchEnv &env) {
 }  // namespace
 
 bool tc_supported(const Problem &p, std::string *why) {
+    if (p.net != NQS_NET_SILU) { *why = "the tensor-core path runs the SiLU network family"; return false; }
     if (p.C != 16 && p.C != 32) { *why = "the tensor-core path needs 16 or 32 channels"; return false; }
     return true;
 }

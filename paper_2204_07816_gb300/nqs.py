@@ -35,7 +35,7 @@ class nqs_problem(ctypes.Structure):
     _fields_ = [('model', ctypes.c_int32), ('L', ctypes.c_int32), ('J1', ctypes.c_double), ('J2', ctypes.c_double),
                 ('t', ctypes.c_double), ('J', ctypes.c_double), ('n_up', ctypes.c_int32),
                 ('n_down', ctypes.c_int32), ('sign_rule', ctypes.c_int32), ('n_layers', ctypes.c_int32),
-                ('channels', ctypes.c_int32)]
+                ('channels', ctypes.c_int32), ('net', ctypes.c_int32)]
 
 
 class NQSError(RuntimeError):
@@ -111,15 +111,18 @@ def _prec(p):
     return PRECISION[p] if isinstance(p, str) else int(p)
 
 
+NET = {'silu': 0, 'cnn1': 1, 'cnn2': 2}
+
+
 def make_problem(model='j1j2', L=4, J1=1.0, J2=0.5, t=1.0, J=0.4, n_up=None, n_down=None, sign_rule=False,
-                 n_layers=2, channels=4):
+                 n_layers=2, channels=4, net='silu'):
     N = L * L
     if n_up is None:
         n_up = N // 2
     if n_down is None:
         n_down = N - n_up
     return nqs_problem(MODEL[model] if isinstance(model, str) else int(model), L, J1, J2, t, J, n_up, n_down,
-                       int(bool(sign_rule)), n_layers, channels)
+                       int(bool(sign_rule)), n_layers, channels, NET[net] if isinstance(net, str) else int(net))
 
 
 def nqs_param_count(problem):

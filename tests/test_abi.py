@@ -98,3 +98,18 @@ def test_checked_build_exports_the_same_entry_points(nqs):
     lib = ctypes.CDLL(path)
     for name in sorted(_declared()):
         assert hasattr(lib, name), name
+
+
+def test_param_count_of_the_paper_families_matches_the_oracle():
+    from oracle import cnn_paper
+    from paper_2204_07816_gb300 import build, nqs
+    build.build()
+    for kind in ('cnn1', 'cnn2'):
+        for model, c_in in (('j1j2', 1), ('tj', 3)):
+            for L, C, B in ((4, 4, 2), (10, 16, 6), (12, 32, 6)):
+                N = L * L
+                prob = (nqs.make_problem('j1j2', L, n_layers=B, channels=C, net=kind) if model == 'j1j2' else
+                        nqs.make_problem('tj', L, n_up=N // 2 - 1, n_down=N // 2 - 1, n_layers=B, channels=C, net=kind))
+                assert nqs.nqs_param_count(prob) == cnn_paper.param_count(cnn_paper.PaperSpec(kind, L, c_in, C, B))
+    assert nqs.nqs_param_count(nqs.make_problem('j1j2', 5, n_up=13, n_down=12, net='cnn1')) == -1   # odd N
+    assert nqs.nqs_param_count(nqs.make_problem('j1j2', 4, net=7)) == -1

@@ -190,3 +190,92 @@ def test_update_with_the_wrong_sign(monkeypatch):
     """theta + eta delta: the exact SR run no longer lowers the energy."""
     monkeypatch.setattr(sr, 'update', lambda params, delta, lr: np.asarray(params) + lr * np.asarray(delta))
     _fails(sr_pins.test_exact_sr_descends_toward_the_ground_state)
+
+
+# ------------------------------------------------------------ the paper's CNN1 / CNN2
+from oracle import cnn_paper  # noqa: E402
+from tests import test_oracle_paper_nets as paper_pins  # noqa: E402
+
+
+def test_transposed_conv_taps_swapped(monkeypatch):
+    """CNN1's transposed convolution writing tap 1 to the even site and tap 0
+    to the odd one: the explicit-loop comparison fails."""
+    real = cnn_paper.tconv
+
+    def swapped(V, T, gamma, kind):
+        return real(V, T[:, :, ::-1], gamma, kind) if kind == 'cnn1' else real(V, T, gamma, kind)
+    monkeypatch.setattr(cnn_paper, 'tconv', swapped)
+    _fails(paper_pins.test_forward_equals_explicit_loops_and_direct_product, 'cnn1', 1)
+
+
+def test_stride_one_pool_looks_backwards(monkeypatch):
+    """CNN2's stride-one pooling over (s - 1, s) instead of (s, s + 1): the
+    explicit-loop comparison fails."""
+    real = cnn_paper.pool
+
+    def backwards(U, kind):
+        if kind == 'cnn2':
+            a, b = U, np.roll(U, 1, axis=-1)
+            first = a >= b
+            return np.where(first, a, b), first
+        return real(U, kind)
+    monkeypatch.setattr(cnn_paper, 'pool', backwards)
+    _fails(paper_pins.test_forward_equals_explicit_loops_and_direct_product, 'cnn2', 1)
+
+
+def test_product_sign_dropped(monkeypatch):
+    """phi = 0 for every configuration (the sign of the product of neurons
+    lost): the direct-product comparison fails, although the enumeration
+    identity, which uses the same amplitudes on both sides, would not."""
+    real = cnn_paper.forward
+
+    def unsigned(params, configs, spec, return_cache=False):
+        out = real(params, configs, spec, return_cache)
+        return (out[0], np.zeros_like(out[1])) + tuple(out[2:])
+    monkeypatch.setattr(cnn_paper, 'forward', unsigned)
+    _fails(paper_pins.test_forward_equals_explicit_loops_and_direct_product, 'cnn1', 1)
+
+
+def test_pool_gradient_to_both_elements(monkeypatch):
+    """Max-pooling backward routing every window's gradient to its first
+    element: the finite-difference comparison fails."""
+    real = cnn_paper.pool
+
+    def both(U, kind):
+        V, first = real(U, kind)
+        return V, np.ones_like(first) if kind == 'cnn1' else first
+    monkeypatch.setattr(cnn_paper, 'pool', both)
+    # forward unchanged (V is the max); the backward now routes every gV to the first element
+    _fails(paper_pins.test_backward_matches_central_differences, 'cnn1', 1)
+
+
+def test_embedding_rows_exchanged(monkeypatch):
+    """CNN2's embedding reading up spins from the down row: the explicit-loop
+    comparison fails."""
+    real = cnn_paper.state_index
+    monkeypatch.setattr(cnn_paper, 'state_index', lambda configs, spec: 1 - real(configs, spec)
+                        if spec.c_in == 1 else real(configs, spec))
+    _fails(paper_pins.test_forward_equals_explicit_loops_and_direct_product, 'cnn2', 1)
+
+
+def test_padding_adjoint_without_wrap(monkeypatch):
+    """The adjoint of the periodic padding dropping the wrapped contributions
+    (the PBC gradient of Sec. 5.4.2 without its accumulation): the
+    finite-difference comparison fails."""
+    real = cnn_paper._conv_backward
+
+    def open_boundary(gU, X, W):
+        dW, db, dX = real(gU, X, W)
+        L = X.shape[-1]
+        dX_open = np.zeros_like(dX)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                sh = cnn.shifted(gU, -dy, -dx)
+                mask = np.zeros((L, L))
+                ys = slice(max(0, dy), L + min(0, dy))
+                xs = slice(max(0, dx), L + min(0, dx))
+                mask[ys, xs] = 1.0
+                dX_open += np.einsum('oc,boyx->bcyx', W[:, :, dy + 1, dx + 1], sh) * mask
+        return dW, db, dX_open
+    monkeypatch.setattr(cnn_paper, '_conv_backward', open_boundary)
+    _fails(paper_pins.test_backward_matches_central_differences, 'cnn2', 1)
