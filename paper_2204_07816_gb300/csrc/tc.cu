@@ -57,6 +57,15 @@ constexpr int kTcThreads = 32 * (kMaxEpiWarps + kIssuers);
 template <int C> constexpr int kMinBlocks = C == 16 ? 2 : 1;
 constexpr int kMaxTiles = 16;
 constexpr int kPropWindow = 16;   // sampler: proposal steps drawn at once
+constexpr int kPropWindowOne = 64;   // the same with one chain per block (one draw per thread either way)
+__host__ __device__ inline int prop_window(int per_block) { return per_block == 1 ? kPropWindowOne : kPropWindow; }
+
+// A configuration read with two sites exchanged (the sampler's proposal),
+// in place of the group's copy in shared memory (one-configuration groups).
+struct SwapSrc {
+    const int8_t *cfg;
+    int i, j;
+};
 constexpr int kMaxSlots = 2;
 constexpr uint32_t kNone = 0xFFFFu;
 
@@ -69,7 +78,7 @@ struct TcPlan {
     // images of layer 0 (K0 x C) and of every later layer (9 x C x C)
     uint32_t f32_count, f32_bytes;
     // shared-memory offsets; act holds slots x 2 buffers of act_bytes (row form: one buffer)
-    uint32_t o_act, o_w0, o_w1, o_f32, o_rowtab, o_sitetab, o_spad, o_spins, o_res, o_bar, o_extra, total;
+    uint32_t o_act, o_w0, o_w1, o_f32, o_rowtab, o_sitetab, o_spins, o_res, o_bar, o_extra, total;
     // row form (rows = 1, local energies): activations [kc][(xp * Lp + yp) * G + g][16 B] updated in place,
     // rows_total rows per plane; a 4 KB zero block; the MMA lists; the layer images of layers >= 1 sit wimg
     // bytes after the tap-form images
@@ -99,7 +108,6 @@ struct TcShared {
     uint32_t *tmem_addr;
     int *abort_flag;
     int8_t *spins;               // [slots][G][N] the groups' configurations
-    int8_t *spad;                // [slots][Lp * Lp * G] padded copies, row = pos * G + g
     const uint2 *rowtab;         // [n_tiles * 128] destination rows of each output row
     const uint2 *sitetab;        // [N] padded positions of each site (main + images)
     float *f32;                  // biases [n_layers][C], head [2][C]
@@ -245,26 +253,15 @@ __device__ __forceinline__ void store_rows(const TcPlan &pl, uint32_t act, uint2
     }
 }
 
-// Spins of a slot to the padded lattice, then the layer-0 im2col matrix
-// (row = output row, K0 columns: tap-major, one-hot channel minor; zero
-// padded) into the slot's second activation buffer.
-__device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot, const Band &band) {
-    const int G = pl.G;
-    int8_t *spad = sh.spad + slot * pl.Lp * pl.Lp * G;
-    const int8_t *spins = sh.spins + slot * G * pl.N;
-    for (int r = threadIdx.x; r < G * pl.N; r += blockDim.x) {
-        const int g = r / pl.N, site = r - g * pl.N;
-        const uint2 pos = sh.sitetab[site];
-        const int8_t v = spins[r];
-        const uint32_t d[4] = {pos.x & 0xFFFFu, pos.x >> 16, pos.y & 0xFFFFu, pos.y >> 16};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (d[i] != kNone) spad[d[i] * G + g] = v;
-    }
-    __syncthreads();
-    int offg[9];
-#pragma unroll
-    for (int o = 0; o < 9; ++o) offg[o] = ((o / 3 - 1) * pl.Lp + (o % 3 - 1)) * G;
+// Layer-0 im2col matrix of a slot (row = output row, K0 columns: tap-major,
+// one-hot channel minor; zero padded) into the slot's second activation
+// buffer. Each interior output row reads its 3 x 3 neighbourhood straight
+// from the configuration (periodic wrap by index arithmetic).
+__device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot, const Band &band,
+                           const SwapSrc *swap = nullptr) {
+    const int G = pl.G, L = pl.L, Lp = pl.Lp;
+    const int8_t *spins = swap ? swap->cfg : sh.spins + slot * G * pl.N;
+    const int si = swap ? swap->i : -1, sj = swap ? swap->j : -1;
     const uint32_t a0 = act_addr(pl, sh, slot, 1);
     const uint32_t one = 0x3F80u, minus_one = 0xBF80u;   // bf16 +1, -1
     int t0, t1;
@@ -276,19 +273,30 @@ __device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot, const
 #pragma unroll
         for (int i = 0; i < 16; ++i) w[i] = 0u;
         if (main != kNone) {
+            const int pos = (int)main / G, g = (int)main - pos * G;
+            const int y = pos / Lp - 1, x = pos - (y + 1) * Lp - 1;
+            const int8_t *sp = spins + g * pl.N;
+            const int yr[3] = {(y == 0 ? L - 1 : y - 1) * L, y * L, (y == L - 1 ? 0 : y + 1) * L};
+            const int xc[3] = {x == 0 ? L - 1 : x - 1, x, x == L - 1 ? 0 : x + 1};
+            int sv[9];
 #pragma unroll
             for (int o = 0; o < 9; ++o) {
-                const int s = spad[(int)main + offg[o]];
+                const int site = yr[o / 3] + xc[o % 3];
+                sv[o] = sp[site == si ? sj : (site == sj ? si : site)];
+            }
+#pragma unroll
+            for (int o = 0; o < 9; ++o) {
+                const int sval = sv[o];
                 if (pl.c_in == 1) {
-                    const uint32_t b = s > 0 ? one : minus_one;
-                    w[o >> 1] |= b << (16 * (o & 1));
+                    const uint32_t bv = sval > 0 ? one : minus_one;
+                    w[o >> 1] |= bv << (16 * (o & 1));
                 } else {
                     // one-hot channel (hole, up, down) = column 3 o + channel; every index is a
                     // compile-time constant, so w stays in registers
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
                         const int k = 3 * o + ch;
-                        const bool hit = ch == 0 ? s == 0 : (ch == 1 ? s == 1 : s == -1);
+                        const bool hit = ch == 0 ? sval == 0 : (ch == 1 ? sval == 1 : sval == -1);
                         if (hit) w[k >> 1] |= one << (16 * (k & 1));
                     }
                 }
@@ -303,18 +311,21 @@ __device__ void build_slot(const TcPlan &pl, const TcShared &sh, int slot, const
     __syncthreads();
 }
 
-// Issue the MMAs of layer l for one slot (issuer threads only).
+// Issue the MMAs of layer l for one slot (issuer warps: the whole warp runs
+// the loop, one elected lane issues).
 template <int C>
 __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int slot,
                             int l, int *err, const Band &band) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = st.wseq + (uint32_t)l;
     const int iw = warp - pl.epi;   // issuer index
-    if (lane == 0 && iw >= 0 && iw < kIssuers) {
-        if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
-            // the last slot prefetches the next load into the other buffer:
-            // its previous user (load q - 1) has completed for every slot
-            if (iw == 0 && slot == pl.slots - 1) issue_weight_load(pl, sh, packed, q + 1, st.wbase);
+    if (iw >= 0 && iw < kIssuers) {
+        if (__all_sync(0xffffffffu, wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag))) {
+            // the last slot prefetches the next load into the other buffer (its previous user, load q - 1, has
+            // completed for every slot); the last issuer does it, so issuer 0's MMAs start at once (a one-tile
+            // plan leaves that warp free; the bulk copy takes about 370 cycles to issue)
+            if (lane == 0 && iw == kIssuers - 1 && slot == pl.slots - 1)
+                issue_weight_load(pl, sh, packed, q + 1, st.wbase);
             ptx::tc_fence_after();
             const uint32_t tmem = *sh.tmem_addr + (uint32_t)(slot * pl.slot_cols);
             const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
@@ -327,9 +338,9 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
                 for (int t = t0 + iw; t < t1; t += kIssuers) {
                     const uint32_t arow = (uint32_t)(pl.r0 + t * 128);
                     for (int kk = 0; kk < pl.K0 / 16; ++kk)
-                        ptx::mma_bf16(tmem + (uint32_t)(t * C), a_base + ((arow * 16u + (uint32_t)(2 * kk) * pl.plane) >> 4),
+                        ptx::mma_bf16_elect(tmem + (uint32_t)(t * C), a_base + ((arow * 16u + (uint32_t)(2 * kk) * pl.plane) >> 4),
                                       b_base + (uint64_t)((2 * kk * C * 16) >> 4), idesc, kk ? 1u : 0u);
-                    ptx::mma_commit(&sh.bar_tile[slot * kMaxTiles + t]);
+                    ptx::mma_commit_elect(&sh.bar_tile[slot * kMaxTiles + t]);
                 }
             } else {
                 const uint64_t a_base = ptx::smem_desc(act_addr(pl, sh, slot, (l - 1) & 1), pl.plane, 128);
@@ -345,13 +356,13 @@ __device__ void issue_layer(const TcPlan &pl, const TcShared &sh, const unsigned
                         for (int kk = 0; kk < C / 16; ++kk) {
                             const uint64_t ad = a_base + ((arow * 16u + (uint32_t)(2 * kk) * pl.plane) >> 4);
                             const uint64_t bd = b_base + (uint64_t)(((o * (C / 8) + 2 * kk) * C * 16) >> 4);
-                            ptx::mma_bf16(d, ad, bd, idesc, (o | kk) ? 1u : 0u);
+                            ptx::mma_bf16_elect(d, ad, bd, idesc, (o | kk) ? 1u : 0u);
                         }
                     }
-                    ptx::mma_commit(&sh.bar_tile[slot * kMaxTiles + t]);
+                    ptx::mma_commit_elect(&sh.bar_tile[slot * kMaxTiles + t]);
                 }
             }
-        } else {
+        } else if (lane == 0) {
             raise_abort(sh, err);
         }
     }
@@ -474,12 +485,13 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
                     cp = fmaf(pp[k], hv, cp);
                 }
             }
-            // configuration-major ([a | phi][g][padded position p], row = p * G + g), so that the head's
-            // reads of one configuration's sites are consecutive words
+            // configuration-major in site order ([a | phi][g][y L + x]), so that the head reads one
+            // configuration's sites as consecutive words
             const uint32_t pos = main / (uint32_t)pl.G, g = main - pos * (uint32_t)pl.G;
-            const uint32_t idx = g * (uint32_t)Lp2 + pos;
+            const uint32_t yy = pos / (uint32_t)pl.Lp - 1u, xx = pos - (yy + 1u) * (uint32_t)pl.Lp - 1u;
+            const uint32_t idx = g * (uint32_t)pl.N + yy * (uint32_t)pl.L + xx;
             contrib[idx] = ca;
-            contrib[(uint32_t)(pl.G * Lp2) + idx] = cp;
+            contrib[(uint32_t)(pl.G * pl.N) + idx] = cp;
         }
     }
     if (!ok) raise_abort(sh, err);
@@ -491,10 +503,12 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
     return *(volatile int *)sh.abort_flag == 0;
 }
 
-// a[g] = sum over sites of the head contributions (one warp per g, fixed order).
-// contrib: [a | phi][g][padded position], as the last layer's epilogue stores them.
+// a[g] = sum over sites of the head contributions (one warp per g, fixed
+// order: lane k sums sites k, k + 32, ... in order, then an xor-shuffle tree).
+// contrib: [a | phi][g][site y L + x], as the last layer's epilogue stores
+// them; roll: rows by which each configuration was rolled (or null).
 __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const int *roll, const float *contrib) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G, Lp2 = pl.Lp * pl.Lp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G, N = pl.N;
     double *res = sh.res + slot * 2 * G;
     for (int g = warp; g < G; g += (int)(blockDim.x >> 5)) {
         float sa = 0.f, sp = 0.f;
@@ -506,9 +520,9 @@ __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const 
                 const int y = site / pl.L, x = site - y * pl.L;
                 cs = ((y - rg + pl.L) % pl.L) * pl.L + x;
             }
-            const int idx = g * Lp2 + (int)(sh.sitetab[cs].x & 0xFFFFu);
+            const int idx = g * N + cs;
             sa += contrib[idx];
-            sp += contrib[G * Lp2 + idx];
+            sp += contrib[G * N + idx];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -531,9 +545,9 @@ __device__ void head_slot(const TcPlan &pl, const TcShared &sh, int slot, const 
 template <int C>
 __device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int *err,
                            const Band &band = dense_band(), const unsigned char *cache = nullptr,
-                           unsigned char *cache_w = nullptr) {
+                           unsigned char *cache_w = nullptr, const SwapSrc *swap = nullptr) {
     for (int s = 0; s < pl.slots; ++s) {
-        build_slot(pl, sh, s, band);
+        build_slot(pl, sh, s, band, swap);
         issue_layer<C>(pl, sh, packed, st, s, 0, err, band);
     }
     for (int l = 0; l < pl.n_layers; ++l) {
@@ -665,7 +679,8 @@ __device__ void build_rows(const TcPlan &pl, const TcShared &sh) {
     __syncthreads();
 }
 
-// Issue layer l's MMAs (issuer threads only): issuer iw owns output columns
+// Issue layer l's MMAs (issuer warps: the whole warp runs the loop, one
+// elected lane issues): issuer iw owns output columns
 // x in [iw L / kIssuers, (iw + 1) L / kIssuers) and commits to bar_tile[iw].
 template <int C>
 __device__ void row_issue(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int l,
@@ -673,9 +688,8 @@ __device__ void row_issue(const TcPlan &pl, const TcShared &sh, const unsigned c
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = st.wseq + (uint32_t)l;
     const int iw = warp - pl.epi;
-    if (lane == 0 && iw >= 0 && iw < kIssuers) {
-        if (wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag)) {
-            if (iw == 0) issue_weight_load(pl, sh, packed, q + 1, st.wbase);
+    if (iw >= 0 && iw < kIssuers) {
+        if (__all_sync(0xffffffffu, wait_or_abort(&sh.bar_w[q & 1], (q >> 1) & 1, sh.abort_flag))) {
             ptx::tc_fence_after();
             const uint32_t tmem = *sh.tmem_addr;
             const uint32_t wb = ptx::smem_u32(sh.base + ((q & 1) ? pl.o_w1 : pl.o_w0));
@@ -687,24 +701,27 @@ __device__ void row_issue(const TcPlan &pl, const TcShared &sh, const unsigned c
                 const int n0 = cnt[1];
                 for (int k = 0; k < n0; ++k) {
                     const uint4 e = tab[kMtabLayer + k];
-                    ptx::mma_bf16(tmem + (e.z & 0x7FFFFFFFu), ((uint64_t)kDescHi << 32) | e.x,
+                    ptx::mma_bf16_elect(tmem + (e.z & 0x7FFFFFFFu), ((uint64_t)kDescHi << 32) | e.x,
                                   ((uint64_t)kDescHi << 32) | (e.y + wlo), e.w, e.z >> 31);
                 }
             } else {
                 // zero this issuer's accumulators: A = B = the zero block, N = its columns
                 const int xa = iw * pl.L / kIssuers, xb = (iw + 1) * pl.L / kIssuers;
                 const uint64_t z = ((uint64_t)kDescHi << 32) | desc_lo(ptx::smem_u32(sh.base + pl.o_zero), 2048);
-                ptx::mma_bf16(tmem + (uint32_t)(xa * C), z, z, ptx::idesc_bf16(128, (xb - xa) * C), 0u);
+                ptx::mma_bf16_elect(tmem + (uint32_t)(xa * C), z, z, ptx::idesc_bf16(128, (xb - xa) * C), 0u);
                 const int n = cnt[0];
 #pragma unroll 4
                 for (int k = 0; k < n; ++k) {
                     const uint4 e = tab[k];
-                    ptx::mma_bf16(tmem + e.z, ((uint64_t)kDescHi << 32) | e.x, ((uint64_t)kDescHi << 32) | (e.y + wlo),
+                    ptx::mma_bf16_elect(tmem + e.z, ((uint64_t)kDescHi << 32) | e.x, ((uint64_t)kDescHi << 32) | (e.y + wlo),
                                   e.w, 1u);
                 }
             }
-            ptx::mma_commit(&sh.bar_tile[iw]);
-        } else {
+            ptx::mma_commit_elect(&sh.bar_tile[iw]);
+            // next layer's weights into the other buffer (last read by layer q - 1's MMAs, completed), after
+            // this layer's MMAs are issued
+            if (lane == 0 && iw == 0) issue_weight_load(pl, sh, packed, q + 1, st.wbase);
+        } else if (lane == 0) {
             raise_abort(sh, err);
         }
     }
@@ -843,32 +860,6 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
     return *(volatile int *)sh.abort_flag == 0;
 }
 
-// a[g] = sum over sites of the head contributions, stored in site order
-// [a | phi][g][site]: the sites and the reduction tree of head_slot (lane k
-// sums sites k, k + 32, ... in order, then an xor-shuffle tree), so the
-// result is bitwise the tap form's.
-__device__ void row_head(const TcPlan &pl, const TcShared &sh) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = pl.G, N = pl.N;
-    const float *contrib = reinterpret_cast<const float *>(sh.base + pl.o_act);
-    for (int g = warp; g < G; g += (int)(blockDim.x >> 5)) {
-        float sa = 0.f, sp = 0.f;
-        for (int site = lane; site < N; site += 32) {
-            sa += contrib[g * N + site];
-            sp += contrib[G * N + g * N + site];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sa += __shfl_xor_sync(0xffffffffu, sa, o);
-            sp += __shfl_xor_sync(0xffffffffu, sp, o);
-        }
-        if (lane == 0) {
-            sh.res[g] = (double)sa;
-            sh.res[G + g] = (double)sp;
-        }
-    }
-    __syncthreads();
-}
-
 // Evaluate the group's G configurations (sh.spins) in the row form; results
 // in sh.res. False if a wait timed out (the block must stop).
 template <int C>
@@ -878,7 +869,7 @@ __device__ bool row_forward(const TcPlan &pl, const TcShared &sh, const unsigned
     for (int l = 0; l < pl.n_layers; ++l) {
         if (!row_epilogue<C>(pl, sh, st, l, err)) return false;
         if (l + 1 < pl.n_layers) row_issue<C>(pl, sh, packed, st, l + 1, err);
-        else row_head(pl, sh);
+        else head_slot(pl, sh, 0, nullptr, reinterpret_cast<const float *>(sh.base + pl.o_act));
     }
     st.wseq += (uint32_t)pl.n_layers;
     return true;
@@ -918,7 +909,6 @@ __device__ void tc_init(TcShared &sh, unsigned char *smem, uint32_t tmem_cols, T
 __device__ void tc_bind(const TcPlan &pl, TcShared &sh, const unsigned char *packed, TcState &st) {
     unsigned char *smem = sh.base;
     sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
-    sh.spad = reinterpret_cast<int8_t *>(smem + pl.o_spad);
     sh.rowtab = reinterpret_cast<const uint2 *>(smem + pl.o_rowtab);
     sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
     sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
@@ -945,11 +935,10 @@ __device__ void tc_bind(const TcPlan &pl, TcShared &sh, const unsigned char *pac
         const int n = images(pl.L, pl.Lp, s % pl.L, s / pl.L, pos);
         sitetab[s] = pack4(pos, n);
     }
-    // zero the activation buffers and padded spins: rows outside the lattice
-    // are read by discarded output rows only, but keep them finite
+    // zero the activation buffers: rows outside the lattice are read by
+    // discarded output rows only, but keep them finite
     for (uint32_t i = threadIdx.x; i < pl.slots * 2 * pl.act_bytes / 4; i += blockDim.x)
         reinterpret_cast<uint32_t *>(smem + pl.o_act)[i] = 0u;
-    for (uint32_t i = threadIdx.x; i < (uint32_t)(pl.slots * pl.Lp * pl.Lp * pl.G); i += blockDim.x) sh.spad[i] = 0;
     ptx::fence_async_smem();
     __syncthreads();
     st.wbase = st.wissued;
@@ -963,7 +952,6 @@ __device__ void tc_bind(const TcPlan &pl, TcShared &sh, const unsigned char *pac
 __device__ void row_bind(const TcPlan &pl, TcShared &sh, const unsigned char *packed, TcState &st) {
     unsigned char *smem = sh.base;
     sh.spins = reinterpret_cast<int8_t *>(smem + pl.o_spins);
-    sh.spad = nullptr;
     sh.rowtab = nullptr;
     sh.sitetab = reinterpret_cast<const uint2 *>(smem + pl.o_sitetab);
     sh.f32 = reinterpret_cast<float *>(smem + pl.o_f32);
@@ -1325,15 +1313,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     // proposals of the next kPropWindow steps of every chain of the group,
     // drawn in parallel (they do not depend on the chain state): site i,
     // neighbour j and log u, [step][chain]
+    const int W = prop_window(per_block);
     double *wlu = cphi + per_block;
-    int *wpi = reinterpret_cast<int *>(wlu + kPropWindow * per_block);
-    int *wpj = wpi + kPropWindow * per_block;
+    int *wpi = reinterpret_cast<int *>(wlu + W * per_block);
+    int *wpj = wpi + W * per_block;
     // moves and accepted moves of the block, in shared memory after the proposal window (not live in
     // registers across the forward; the address is recomputed where it is used)
     auto scnt = [&]() {
         return reinterpret_cast<unsigned long long *>(smem + pl.o_extra +
                                                       ((al16(per_block * pl.N) + al16(8 * pl.slots * (pl.G + 1)) +
-                                                        16 * per_block + 16 * kPropWindow * per_block + 7) & ~7u));
+                                                        16 * per_block + 16 * prop_window(per_block) * per_block +
+                                                        7) & ~7u));
     };
     if (threadIdx.x == 0) { scnt()[0] = 0; scnt()[1] = 0; }
     // chain groups: group k = blockIdx.x + j * gridDim.x (one pass when the
@@ -1362,9 +1352,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
     for (int sweep = 0; ok && sweep < n_sweeps; ++sweep) {
         for (int q = 0; q < N; ++q) {
             const int64_t gstep = (int64_t)sweep * N + q;
-            const int w = (int)(gstep % kPropWindow);
+            const int w = (int)(gstep & (int64_t)(W - 1));
             if (w == 0) {   // draw the window (one Philox4x64-10 block per chain and step)
-                for (int t = threadIdx.x; t < kPropWindow * gc; t += blockDim.x) {
+                // every thread has read the previous window (steps without a forward pass no block barrier)
+                __syncthreads();
+                for (int t = threadIdx.x; t < W * gc; t += blockDim.x) {
                     const int ww = t / gc, c = t - ww * gc;
                     if (gstep + ww >= n_steps) continue;
                     const Philox4 b = philox((uint64_t)(c0 + c), step0 + (uint64_t)(gstep + ww), 0, 0, seed, 0);
@@ -1378,6 +1370,31 @@ __global__ void __launch_bounds__(kTcThreads, 2) sample_tc_kernel(TcPlan pl, con
             }
             int *pi_s = wpi + w * per_block;
             int *pj_s = wpj + w * per_block;
+            if (per_block == 1) {
+                // one chain: every thread sees the same state (the last block barrier followed its update), so
+                // each one decides whether the proposal changes it, with no list and no barrier; the forward reads
+                // the chain with the two sites exchanged
+                const int i = pi_s[0], j = pj_s[0];
+                if (!NQS_INDEX_OK(i >= 0 && i < N && j >= 0 && j < N, err) || cur[i] == cur[j]) continue;
+                if (threadIdx.x == 0) scnt()[0] += 1ull;
+                const SwapSrc sw{cur, i, j};
+                if (!tc_forward<C>(pl, sh, packed, st, err, dense_band(), nullptr, nullptr, &sw)) { ok = false; break; }
+                if (threadIdx.x == 0) {
+                    const double an = sh.res[0];
+                    const double delta = 2.0 * (an - ca[0]);
+                    // u < exp(2 (a' - a)) evaluated as log u < 2 (a' - a), log u drawn with the proposal
+                    if (delta >= 0.0 || wlu[w] < delta) {
+                        scnt()[1] += 1ull;
+                        const int8_t t = cur[i];
+                        cur[i] = cur[j];
+                        cur[j] = t;
+                        ca[0] = an;
+                        cphi[0] = sh.res[G];
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
             int *list = list2 + (int)(gstep & 1) * S * (G + 1);
             if (threadIdx.x < S) {   // per-slot list of chains whose proposal changes the state
                 const int s = threadIdx.x;
@@ -1614,7 +1631,6 @@ bool make_plan(const Problem &p, int G, int slots, int ctas, size_t max_smem, in
     pl.o_f32 = o; o = al16(o + pl.f32_count * 4);
     pl.o_rowtab = o; o = al16(o + 8 * pl.n_tiles * 128);
     pl.o_sitetab = o; o = al16(o + 8 * p.N);
-    pl.o_spad = o; o = al16(o + slots * pl.Lp * pl.Lp * G);
     pl.o_spins = o; o = al16(o + slots * G * p.N);
     pl.o_res = o; o = al16(o + 16 * slots * G);
     pl.o_extra = o; o = al16(o + extra_bytes);
@@ -1640,7 +1656,7 @@ int eloc_extra(const Problem &p) {
 
 int sample_extra(const Problem &p, int G, int slots) {
     const int per = G * slots;
-    return (int)(al16(per * p.N) + al16(4 * 2 * (slots * (G + 1))) + 16 * per + 16 * kPropWindow * per + 24);
+    return (int)(al16(per * p.N) + al16(4 * 2 * (slots * (G + 1))) + 16 * per + 16 * prop_window(per) * per + 24);
 }
 
 // Relative throughput of a one-slot plan: useful rows per computed row,
