@@ -127,6 +127,8 @@ ROW_CASES = [
     ('j1j2_10x10', {'L': 7, 'n_up': 25, 'n_down': 24, 'n_layers': 5}),
     ('j1j2_10x10', {'L': 12, 'n_up': 72, 'n_down': 72, 'n_layers': 4}),
     ('j1j2_10x10', {'L': 11, 'n_up': 61, 'n_down': 60, 'n_layers': 3}),
+    ('j1j2_10x10', {'L': 13, 'n_up': 85, 'n_down': 84, 'n_layers': 3}),
+    ('tj_12x12', {'L': 7, 'n_up': 22, 'n_down': 22, 'channels': 16, 'n_layers': 4}),
 ]
 
 
