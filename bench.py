@@ -57,6 +57,9 @@ def parse():
                     help='skip the other workloads (16x16 SR step, t-J 12x12 E_loc, serving mix) after the main line')
     ap.add_argument('--sr-compare', action='store_true',
                     help='time the CG and the sample-space (Woodbury) SR solves on the same O and E_loc')
+    ap.add_argument('--sampler-overlap', action='store_true',
+                    help='serving: requests\' sampler launches on their own streams against one launch over the union '
+                         'of their chains, and against the same launches back to back')
     ap.add_argument('--serve-partition', action='store_true',
                     help='serving mode with per-class SM shares (default: every request sized for the whole GPU)')
     return ap.parse_args()
@@ -137,6 +140,98 @@ def profile_eloc(args):
     ctx.sync()
     print(json.dumps({'mode': 'profile-eloc', 'workload': args.workload, 'samples': args.profile_eloc,
                       'precision': args.precision, 'ms': times, 'samples_per_s': args.profile_eloc / (min(times) / 1e3)}))
+
+
+def sampler_overlap(args):
+    """Sampling in serving, where each request samples on its own stream: K
+    requests of one shape (256 chains each, different parameters) launched
+    concurrently on their streams, against one context sampling the union of
+    their K x 256 chains (what a grouped sampler launch would do, with the plan
+    the launcher picks for that many chains), and against the same K launches
+    back to back; then one request of each shape, concurrent against back to
+    back. Serving's pattern: one launch per sample of every chain, --steps
+    samples. Prints one JSON line per case (best of three, CUDA events)."""
+    import torch
+
+    import nqs_synth
+    from paper_2204_07816_gb300 import build as nbuild
+    from paper_2204_07816_gb300 import nqs
+    nbuild.build()
+    spc = max(1, args.steps)
+    nc = 256
+    shapes = [('j1j2_10x10_c16', 'j1j2', 10, 16, 6), ('tj_12x12_c16', 'tj', 12, 16, 7),
+              ('j1j2_6x6_c32', 'j1j2', 6, 32, 7), ('j1j2_16x16_c32', 'j1j2', 16, 32, 7)]
+
+    def problem(model, L, C, layers):
+        N = L * L
+        if model == 'j1j2':
+            return nqs.make_problem('j1j2', L, J1=1.0, J2=0.5, n_up=N // 2, n_down=N - N // 2, n_layers=layers,
+                                    channels=C)
+        holes = N // 16
+        return nqs.make_problem('tj', L, t=1.0, J=0.4, n_up=(N - holes) // 2, n_down=N - holes - (N - holes) // 2,
+                                n_layers=layers, channels=C)
+
+    def ctx_of(shape, seed, stream):
+        _, model, L, C, layers = shape
+        params = nqs_synth.random_params(1 if model == 'j1j2' else 3, C, layers, seed)
+        return nqs.Context(problem(model, L, C, layers), torch.tensor(params, dtype=torch.float64, device='cuda'),
+                           seed=seed, stream=stream)
+
+    def run(ctxs, chains, serial):
+        """Each context's spc launches on its own stream; serial: each stream waits for the previous one."""
+        cur = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        prev = e0
+        ends = []
+        for ctx, n in zip(ctxs, chains):
+            ctx.stream.wait_event(prev if serial else e0)
+            with torch.cuda.stream(ctx.stream):
+                for _ in range(spc):
+                    ctx.sample(n, 1, 1, 0, 'bf16')
+            ev = torch.cuda.Event()
+            ev.record(ctx.stream)
+            ends.append(ev)
+            prev = ev
+        for ev in ends:
+            cur.wait_event(ev)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def best(ctxs, chains, serial):
+        run(ctxs, chains, serial)    # warm-up (first launch of each plan)
+        return min(run(ctxs, chains, serial) for _ in range(3))
+
+    for shape in shapes:
+        for K in (2, 4):
+            streams = [torch.cuda.Stream() for _ in range(K)]
+            ctxs = [ctx_of(shape, 11 + k, streams[k]) for k in range(K)]
+            union = ctx_of(shape, 11, torch.cuda.Stream())
+            t_conc = best(ctxs, [nc] * K, False)
+            t_seq = best(ctxs, [nc] * K, True)
+            t_union = best([union], [K * nc], False)
+            t_one = best(ctxs[:1], [nc], False)
+            plan1 = nqs.tc_plan(ctxs[0].problem, 'sample', nc)
+            planK = nqs.tc_plan(ctxs[0].problem, 'sample', K * nc)
+            print(json.dumps({'case': shape[0], 'requests': K, 'chains_each': nc, 'samples_per_chain': spc,
+                              'one_request_ms': round(t_one, 3), 'concurrent_streams_ms': round(t_conc, 3),
+                              'back_to_back_ms': round(t_seq, 3), 'union_launch_ms': round(t_union, 3),
+                              'union_over_streams': round(t_union / t_conc, 3),
+                              'plan_one': {k: plan1[k] for k in ('G', 'blocks_per_sm', 'grid')},
+                              'plan_union': {k: planK[k] for k in ('G', 'blocks_per_sm', 'grid')}}), flush=True)
+            for c in ctxs + [union]:
+                c.close()
+    streams = [torch.cuda.Stream() for _ in shapes]
+    ctxs = [ctx_of(sh, 21 + k, streams[k]) for k, sh in enumerate(shapes)]
+    t_conc = best(ctxs, [nc] * len(ctxs), False)
+    t_seq = best(ctxs, [nc] * len(ctxs), True)
+    alone = [best([c], [nc], False) for c in ctxs]
+    print(json.dumps({'case': 'mixed: ' + ', '.join(sh[0] for sh in shapes), 'chains_each': nc,
+                      'samples_per_chain': spc, 'alone_ms': [round(t, 3) for t in alone],
+                      'concurrent_streams_ms': round(t_conc, 3), 'back_to_back_ms': round(t_seq, 3)}), flush=True)
+    for c in ctxs:
+        c.close()
 
 
 def sr_compare(args):
@@ -693,6 +788,9 @@ def main():
         return
     if args.sr_compare:
         sr_compare(args)
+        return
+    if args.sampler_overlap:
+        sampler_overlap(args)
         return
     # the oracle's process pool is started before the first GPU call
     rank = int(os.environ.get('RANK', '0'))

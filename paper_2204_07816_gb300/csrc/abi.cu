@@ -114,6 +114,7 @@ LaunchEnv env_of(nqs_ctx *c) {
     LaunchEnv e;
     e.stream = c->stream;
     e.num_sms = sms_of(c);
+    e.sm_limited = e.num_sms < c->num_sms;
     e.max_smem = c->max_smem;
     e.err = c->err_dev;
     e.moves = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->err_dev) + 16);

@@ -14,6 +14,7 @@ namespace nqs {
 struct LaunchEnv {
     cudaStream_t stream;
     int num_sms;
+    bool sm_limited = false;   // num_sms is the context's SM share (nqs_set_sm_limit): grids stay within it
     size_t max_smem;     // opt-in shared memory per block
     int *err;            // device error bits
     unsigned long long *moves = nullptr;   // sampler counters [2]: moves that change the state, accepted moves

@@ -1883,21 +1883,37 @@ int launch_eloc_tc_multi(const TcMultiItem *items, int count, void *dev_table, i
 
 namespace {
 
-// Sampler plan: chains per block so that the blocks cover the SMs, one group
-// in flight (with one or two chains per block a second slot only adds fixed
-// per-forward costs). With at most two chains per SM, two co-resident blocks
-// of one chain each (measured on GB300: 1.3-1.4x faster than one block of two
-// chains, since a forward of one or two configurations is latency-bound and
-// the blocks overlap their layer boundaries).
-bool sample_plan(const Problem &p, int n_chains, size_t max_smem, int num_sms, TcPlan *out, std::string *why) {
-    int ctas = (n_chains + num_sms - 1) / num_sms <= 2 ? 2 : 1;
+// Sampler plan: one chain per block, with as many co-resident blocks per SM
+// as fit (three, two or one); chains beyond one wave of blocks run in later
+// waves that the hardware schedules as blocks retire. A forward of one
+// configuration is latency-bound and co-resident blocks overlap their layer
+// boundaries: measured on GB300, two blocks of one chain were 1.3-1.4x faster
+// than one block of two chains, and for 512 to 4,096 chains one chain per
+// block (three blocks per SM where they fit) ran 1.3-1.8x faster at 10x10,
+// 1.2-2.0x at t-J 12x12 and 1.3-1.7x at 16x16 with 32 channels than the
+// earlier plans of 3 to 10 chains per block at one block per SM (the chains
+// are the same bit for bit: a configuration's log psi does not depend on its
+// row in the tile).
+bool sample_plan(const Problem &p, size_t max_smem, TcPlan *out, std::string *why) {
     int fg = 0, fs = 0, fc = 1;
     const char *force = getenv("NQS_TC_SAMPLE");   // "G,slots,blocks per SM" (tuning)
-    if (force && sscanf(force, "%d,%d,%d", &fg, &fs, &fc) == 3 && fc >= 1 && fc <= 2) ctas = fc;
-    for (; ctas >= 1; --ctas) {   // one block per SM if two do not fit
-        const int want = std::max(1, (n_chains + num_sms * ctas - 1) / (num_sms * ctas));
-        const int slots = fg > 0 ? std::min(std::max(fs, 1), kMaxSlots) : (want >= 8 ? 2 : 1);
-        for (int G = fg > 0 ? std::min(fg, 16) : std::min((want + slots - 1) / slots, 16); G >= 1; --G)
+    const bool forced = force && sscanf(force, "%d,%d,%d", &fg, &fs, &fc) == 3 && fc >= 1 && fc <= 3 && fg >= 1;
+    if (!forced) {
+        // the kernel is compiled for two blocks of kTcThreads threads, so it uses at most 96 registers a thread
+        // (65,536 / 640, in steps of 8); a launch of fewer threads leaves room for a third block
+        constexpr int kRegsCap = 65536 / (2 * kTcThreads) / 8 * 8;
+        for (int ctas = 3; ctas >= 1; --ctas)
+            if (make_plan(p, 1, 1, ctas, max_smem, sample_extra(p, 1, 1), out, why)) {
+                // one epilogue warp per TMEM lane quarter (measured 8 % faster than eight warps)
+                if (out->n_tiles <= 4) out->epi = 4;
+                if (ctas * 32 * (out->epi + kIssuers) * kRegsCap > 65536) continue;
+                return true;
+            }
+        return false;
+    }
+    for (int ctas = fc; ctas >= 1; --ctas) {   // fewer blocks per SM if the forced count does not fit
+        const int slots = std::min(std::max(fs, 1), kMaxSlots);
+        for (int G = std::min(fg, 16); G >= 1; --G)
             if (make_plan(p, G, slots, ctas, max_smem, sample_extra(p, G, slots), out, why)) {
                 // a sampler group is one or a few tiles: one epilogue warp per
                 // TMEM lane quarter (measured 8 % faster than eight warps)
@@ -1908,6 +1924,15 @@ bool sample_plan(const Problem &p, int n_chains, size_t max_smem, int num_sms, T
     return false;
 }
 
+// Sampler grid: one block per chain group, or, when the groups outnumber the
+// co-resident blocks and a group holds several chains or the context is held
+// to an SM share, the co-resident blocks, each taking several groups in turn.
+int64_t sample_grid(const TcPlan &pl, int64_t n_chains, int num_sms, bool sm_limited) {
+    const int64_t per = (int64_t)pl.G * pl.slots, groups = (n_chains + per - 1) / per;
+    if (per == 1 && !sm_limited) return groups;
+    return std::min<int64_t>(groups, (int64_t)num_sms * pl.ctas);
+}
+
 }  // namespace
 
 int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_t *chains, int n_chains,
@@ -1915,12 +1940,12 @@ int launch_sample_tc(const Problem &p, const double *, const void *packed, int8_
                      double *out_logpsi, const LaunchEnv &env) {
     std::string why;
     TcPlan pl;
-    if (!tc_supported(p, &why) || !sample_plan(p, n_chains, env.max_smem, env.num_sms, &pl, &why)) {
+    if (!tc_supported(p, &why) || !sample_plan(p, env.max_smem, &pl, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
     }
     const int per_block = pl.G * pl.slots;
-    const int grid = std::min((n_chains + per_block - 1) / per_block, env.num_sms * pl.ctas);
+    const int grid = (int)sample_grid(pl, n_chains, env.num_sms, env.sm_limited);
     NQS_TC_DISPATCH(p.C, {
         auto k = sample_tc_kernel<CC>;
         if (int rc = prep(k, pl, env)) return rc;
@@ -1942,14 +1967,14 @@ int tc_describe_plan(const Problem &p, int kind, int64_t n, size_t max_smem, int
     TcPlan pl;
     bool ok = tc_supported(p, why);
     if (ok) {
-        if (kind == 2) ok = sample_plan(p, (int)n, max_smem, num_sms, &pl, why);
+        if (kind == 2) ok = sample_plan(p, max_smem, &pl, why);
         else if (kind == 1 && use_row_form(p, max_smem, &pl)) ok = true;
         else ok = best_plan(p, max_smem, kind == 1, 16, 2, &pl, why);
     }
     if (!ok) return NQS_ERR_UNSUPPORTED;
     const int64_t per = (int64_t)pl.G * pl.slots, cap = (int64_t)num_sms * pl.ctas;
     int64_t grid;
-    if (kind == 2) grid = std::min<int64_t>((n + per - 1) / per, cap);
+    if (kind == 2) grid = sample_grid(pl, n, num_sms, false);
     else if (kind == 1) grid = std::max<int64_t>(1, std::min<int64_t>(n, cap));
     else grid = std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, cap));
     out[0] = pl.G;

@@ -31,7 +31,7 @@ def _problem(nqs, w, **over):
 
 
 def _check_fits(plan, channels):
-    assert plan['blocks_per_sm'] in (1, 2)
+    assert plan['blocks_per_sm'] in (1, 2, 3)
     assert plan['epilogue_warps'] % 4 == 0 and plan['epilogue_warps'] >= 4
     assert 1 <= plan['tiles'] <= 16
     assert plan['blocks_per_sm'] * (plan['smem_bytes'] + 1024) <= SM_BYTES
@@ -63,9 +63,8 @@ def test_plans_fit_across_lattice_sizes(nqs, L, channels):
             assert channels == 32 and L >= 24     # too large for one block's shared memory
             continue
         _check_fits(plan, channels)
-        if kind == 'sample':   # every chain group has a block, or the grid fills the SMs and blocks take several
-            groups = -(-n // (plan['G'] * plan['slots']))
-            assert plan['grid'] == min(groups, NUM_SMS * plan['blocks_per_sm'])
+        if kind == 'sample':   # one chain per block, every chain has a block (chains beyond one wave run in later waves)
+            assert (plan['G'], plan['slots'], plan['grid']) == (1, 1, n)
 
 
 def test_measured_choices(nqs):
@@ -83,9 +82,12 @@ def test_measured_choices(nqs):
                                           channels=16), 'local_energy', 4096, MAX_SMEM, NUM_SMS)
         assert pl['row_form'] == want, L
         assert pl['G'] == (min(16, 128 // L) if want else pl['G'])
-    # 256 chains: one chain per block, two blocks per SM
-    s = nqs.tc_plan(p10, 'sample', 256, MAX_SMEM, NUM_SMS)
-    assert (s['G'], s['blocks_per_sm'], s['grid']) == (1, 2, 256)
+    # sampler: one chain per block, three co-resident blocks where they fit; every chain has its block
+    for n in (256, 4096):
+        s = nqs.tc_plan(p10, 'sample', n, MAX_SMEM, NUM_SMS)
+        assert (s['G'], s['slots'], s['blocks_per_sm'], s['grid'], s['epilogue_warps']) == (1, 1, 3, n, 4)
+    p16c32 = nqs.make_problem('j1j2', 16, n_layers=8, channels=32)
+    assert nqs.tc_plan(p16c32, 'sample', 256, MAX_SMEM, NUM_SMS)['blocks_per_sm'] == 2
     # t-J 12x12, 16 channels: two blocks of three configurations
     ptj = nqs.make_problem('tj', 12, n_up=63, n_down=63, n_layers=6, channels=16)
     t = nqs.tc_plan(ptj, 'local_energy', 8192, MAX_SMEM, NUM_SMS)
