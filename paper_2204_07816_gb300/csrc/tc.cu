@@ -596,7 +596,9 @@ constexpr uint32_t kDescHi = (128u >> 4) | (1u << 14);   // SBO = 128 B; bit 46:
 // per kernel row dy and input column xp in [xa, xb + 1], the outputs
 // lo .. hi = max(xp - 2, xa) .. min(xp, xb - 1) with weight blocks from
 // j0 = 2 - xp + lo, K halves innermost: every output sees its taps in the
-// tap form's order (dy, then dx, then K).
+// tap form's order (dy, then dx, then K). The padded columns 0 and L + 1 are
+// the periodic images of columns L and 1, so the A operands are read there
+// and the images are never stored.
 template <int C>
 __device__ void row_build_mtab(const TcPlan &pl, const TcShared &sh, int iw) {
     uint4 *tab = reinterpret_cast<uint4 *>(sh.base + pl.o_mtab) + iw * (kMtabLayer + kMtab0);
@@ -609,7 +611,8 @@ __device__ void row_build_mtab(const TcPlan &pl, const TcShared &sh, int iw) {
         for (int xp = xa; xp <= xb + 1; ++xp) {
             const int lo = max(xp - 2, xa), hi = min(xp, xb - 1);
             const int j0 = 2 - xp + lo;
-            const uint32_t arow = (uint32_t)((xp * pl.Lp + dy) * pl.G);
+            const int xs = xp == 0 ? pl.L : (xp == pl.L + 1 ? 1 : xp);
+            const uint32_t arow = (uint32_t)((xs * pl.Lp + dy) * pl.G);
             for (int kk = 0; kk < C / 16; ++kk) {
                 const uint32_t boff = (uint32_t)(((dy * KC + 2 * kk) * 3 * C + j0 * C) * 16);
                 tab[n++] = make_uint4(desc_lo(act + arow * 16u + (uint32_t)(2 * kk) * pl.plane, pl.plane),
@@ -742,8 +745,9 @@ __device__ __forceinline__ void row_wait(uint32_t (&r)[C / 16][16]) {
 }
 
 // One output column x of one row (y, g): bias + SiLU to bf16, stored at the
-// padded position and its periodic images; or, after the last layer, the
-// head contributions of the position.
+// padded position and its periodic image along y (the MMAs read the x images
+// from the columns themselves); or, after the last layer, the head
+// contributions of the position.
 template <int C>
 __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *contrib, const float *bias,
                                         const float *wa, const float (&hb)[C == 16 ? C : 1], bool last, int x, int y,
@@ -761,22 +765,17 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
             const float h1 = C == 16 ? hb[(2 * c + 1) % HB] : 0.5f * bias[2 * c + 1];
             w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
         }
-        const int ximg = x == 0 ? L + 1 : (x == L - 1 ? 0 : -1);
+        const int xp = x + 1;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int xp = a == 0 ? x + 1 : ximg;
-            if (xp < 0) continue;
+        for (int b = 0; b < 2; ++b) {
+            const int yp = b == 0 ? y + 1 : yimg;
+            if (yp < 0) continue;
+            const uint32_t row = (uint32_t)((xp * Lp + yp) * G + g);
+            if (!NQS_INDEX_OK(row < (uint32_t)pl.rows_total, err)) continue;
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int yp = b == 0 ? y + 1 : yimg;
-                if (yp < 0) continue;
-                const uint32_t row = (uint32_t)((xp * Lp + yp) * G + g);
-                if (!NQS_INDEX_OK(row < (uint32_t)pl.rows_total, err)) continue;
-#pragma unroll
-                for (int kc = 0; kc < KC; ++kc)
-                    ptx::st_shared_v4(act + (uint32_t)kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1],
-                                      w[4 * kc + 2], w[4 * kc + 3]);
-            }
+            for (int kc = 0; kc < KC; ++kc)
+                ptx::st_shared_v4(act + (uint32_t)kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1],
+                                  w[4 * kc + 2], w[4 * kc + 3]);
         }
     } else {
         // the tap form's head arithmetic: c = 0 .. C - 1 in order, 16-byte broadcast loads
