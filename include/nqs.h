@@ -37,8 +37,16 @@
  *   a one-line description.
  * - Precisions: NQS_FP64 and NQS_FP32 run the convolutions on CUDA cores in
  *   that type; NQS_BF16 runs them on the tcgen05 tensor cores with bf16
- *   operands and fp32 accumulation in tensor memory. In every precision the
- *   log-amplitude ratios, E_loc, energies and the SR solve are float64.
+ *   operands and fp32 accumulation in tensor memory. NQS_FP8 (accepted by
+ *   nqs_local_energy only; the other entry points return
+ *   NQS_ERR_INVALID_ARG for it) keeps layer 0 in bf16 and runs layers >= 1
+ *   with e4m3 operands (the FP8 form of Sec. 5.4.1's convolutions: the
+ *   activations saturated to +-448, the weights scaled per output channel
+ *   by their largest magnitude / 448, the scale applied to the fp32
+ *   accumulator), 16-channel networks on lattices whose row-form plan fits
+ *   (nqs_tc_plan reports row_form = 1), else NQS_ERR_UNSUPPORTED. In every
+ *   precision the log-amplitude ratios, E_loc, energies and the SR solve
+ *   are float64.
  */
 #ifndef NQS_H
 #define NQS_H
@@ -63,7 +71,7 @@ typedef enum {
     NQS_ERR_BOUNDS = -8
 } nqs_status;
 
-typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_BF16 = 2 } nqs_precision;
+typedef enum { NQS_FP64 = 0, NQS_FP32 = 1, NQS_BF16 = 2, NQS_FP8 = 3 } nqs_precision;
 
 typedef enum { NQS_MODEL_J1J2 = 0, NQS_MODEL_TJ = 1 } nqs_model;
 
@@ -216,7 +224,8 @@ int nqs_connected(nqs_ctx *ctx, const int8_t *configs, int64_t n, int32_t max_co
  * configs: device int8 [n][N]. logpsi: device float64 [n][2] giving
  * (a, phi) of each configuration, or NULL to have the library recompute it
  * with the same precision as the connected configurations (recommended for
- * NQS_BF16, so that the rounding of numerator and denominator matches).
+ * NQS_BF16, so that the rounding of numerator and denominator matches;
+ * with NQS_FP8 it is always recomputed and logpsi is not read).
  * eloc_out: device float64 [n][2]. */
 int nqs_local_energy(nqs_ctx *ctx, const int8_t *configs, const double *logpsi, int64_t n,
                      double *eloc_out, int32_t precision);

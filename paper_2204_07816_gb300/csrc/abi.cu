@@ -135,7 +135,7 @@ int prepare_params(nqs_ctx *c, int prec, DeviceParams *dp) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(c, e, "convert params");
         ++c->launches;
-    } else if (prec == NQS_BF16) {
+    } else if (prec == NQS_BF16 || prec == NQS_FP8) {
         LaunchEnv env = env_of(c);
         int rc = launch_tc_pack(c->p, c->params, c->packed, env);
         if (rc) return rc;
@@ -390,11 +390,14 @@ int nqs_local_energy(nqs_ctx *c, const int8_t *configs, const double *logpsi, in
     NvtxRange nvtx_range("nqs_local_energy");
     if (int rc = check_ctx(c)) return rc;
     if (n < 0 || (n > 0 && (!configs || !out))) return fail(c, NQS_ERR_INVALID_ARG, "nqs_local_energy: bad arrays");
-    if (!valid_precision(prec)) return fail(c, NQS_ERR_INVALID_ARG, "nqs_local_energy: bad precision");
+    if (!valid_precision(prec) && prec != NQS_FP8)
+        return fail(c, NQS_ERR_INVALID_ARG, "nqs_local_energy: bad precision");
     if (n == 0) return NQS_OK;
     DeviceParams dp;
     if (int rc = prepare_params(c, prec, &dp)) return rc;
     LaunchEnv env = env_of(c);
+    if (prec == NQS_FP8)
+        return launch_eloc_tc(c->p, c->params, c->packed, configs, nullptr, n, out, nullptr, 0, env, true);
     if (prec == NQS_BF16) {
         const size_t cb = tc_eloc_cache_bytes(c->p, c->max_smem, sms_of(c), n);
         if (cb > 0)

@@ -94,7 +94,7 @@ int launch_logpsi_tc(const Problem &p, const double *p64, const void *packed, co
 size_t tc_eloc_cache_bytes(const Problem &p, size_t max_smem, int num_sms, int64_t n);
 int launch_eloc_tc(const Problem &p, const double *p64, const void *packed, const int8_t *configs,
                    const double *logpsi, int64_t n, double *out, void *cache, size_t cache_bytes,
-                   const LaunchEnv &env);
+                   const LaunchEnv &env, bool f8 = false);
 // grouped local energies of several problems with one channel count (tc.cu)
 struct TcMultiItem {
     Problem p;

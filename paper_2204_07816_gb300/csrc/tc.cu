@@ -84,6 +84,10 @@ struct TcPlan {
     // bytes after the tap-form images
     int rows, rows_total;
     uint32_t wimg, o_zero, o_mtab;
+    // weight loads of layers >= 1: bytes per layer (their stride in the packed image); f8: the row form with
+    // e4m3 operands in layers >= 1 (f8bytes per layer image)
+    uint32_t wstride, f8bytes;
+    int f8;
 };
 
 // Row form: per issuer, the MMAs of a layer >= 1 (kMtabLayer entries at
@@ -176,7 +180,7 @@ __device__ __forceinline__ uint32_t act_addr(const TcPlan &pl, const TcShared &s
 }
 
 __device__ __forceinline__ const unsigned char *tc_layer_weights(const TcPlan &pl, const unsigned char *packed, int l) {
-    return packed + pl.f32_bytes + (l == 0 ? 0 : pl.w0bytes + pl.wimg + (size_t)(l - 1) * pl.wbytes);
+    return packed + pl.f32_bytes + (l == 0 ? 0 : pl.w0bytes + pl.wimg + (size_t)(l - 1) * pl.wstride);
 }
 
 // Issue the bulk copy of weight-load number q (layer (q - wbase) mod n_layers).
@@ -184,7 +188,7 @@ __device__ __forceinline__ void issue_weight_load(const TcPlan &pl, const TcShar
                                                   uint32_t q, uint32_t wbase) {
     const int l = (int)((q - wbase) % (uint32_t)pl.n_layers);
     const int b = q & 1;
-    const uint32_t bytes = l == 0 ? pl.w0bytes : pl.wbytes;
+    const uint32_t bytes = l == 0 ? pl.w0bytes : pl.wstride;
     unsigned char *dst = sh.base + (b ? pl.o_w1 : pl.o_w0);
     ptx::mbar_arrive_expect_tx(&sh.bar_w[b], bytes);
     ptx::bulk_g2s(dst, tc_layer_weights(pl, packed, l), bytes, &sh.bar_w[b]);
@@ -607,7 +611,22 @@ __device__ void row_build_mtab(const TcPlan &pl, const TcShared &sh, int iw) {
     const int xa = iw * pl.L / kIssuers, xb = (iw + 1) * pl.L / kIssuers;
     constexpr int KC = C / 8;
     int n = 0;
-    for (int dy = 0; dy < 3; ++dy)
+    if (pl.f8) {
+        // e4m3 (16 channels): per kernel-row pair q and input column, one K = 32 MMA whose two K halves are
+        // kernel rows 2 q and 2 q + 1, G rows apart in the activations (the A operand's K stride); the B image
+        // holds zeros for kernel row 3
+        for (int q = 0; q < 2; ++q)
+            for (int xp = xa; xp <= xb + 1; ++xp) {
+                const int lo = max(xp - 2, xa), hi = min(xp, xb - 1);
+                const int j0 = 2 - xp + lo;
+                const int xs = xp == 0 ? pl.L : (xp == pl.L + 1 ? 1 : xp);
+                const uint32_t arow = (uint32_t)((xs * pl.Lp + 2 * q) * pl.G);
+                const uint32_t boff = (uint32_t)((2 * q * 3 * C + j0 * C) * 16);
+                tab[n++] = make_uint4(desc_lo(act + arow * 16u, (uint32_t)pl.G * 16u), desc_lo(boff, 3 * C * 16),
+                                      (uint32_t)(lo * C), ptx::idesc_e4m3(128, (hi - lo + 1) * C));
+            }
+    }
+    for (int dy = 0; dy < 3 && !pl.f8; ++dy)
         for (int xp = xa; xp <= xb + 1; ++xp) {
             const int lo = max(xp - 2, xa), hi = min(xp, xb - 1);
             const int j0 = 2 - xp + lo;
@@ -685,7 +704,7 @@ __device__ void build_rows(const TcPlan &pl, const TcShared &sh) {
 // Issue layer l's MMAs (issuer warps: the whole warp runs the loop, one
 // elected lane issues): issuer iw owns output columns
 // x in [iw L / kIssuers, (iw + 1) L / kIssuers) and commits to bar_tile[iw].
-template <int C>
+template <int C, bool F8 = false>
 __device__ void row_issue(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int l,
                           int *err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -716,8 +735,12 @@ __device__ void row_issue(const TcPlan &pl, const TcShared &sh, const unsigned c
 #pragma unroll 4
                 for (int k = 0; k < n; ++k) {
                     const uint4 e = tab[k];
-                    ptx::mma_bf16_elect(tmem + e.z, ((uint64_t)kDescHi << 32) | e.x, ((uint64_t)kDescHi << 32) | (e.y + wlo),
-                                  e.w, 1u);
+                    if constexpr (F8)
+                        ptx::mma_e4m3_elect(tmem + e.z, ((uint64_t)kDescHi << 32) | e.x,
+                                            ((uint64_t)kDescHi << 32) | (e.y + wlo), e.w, 1u);
+                    else
+                        ptx::mma_bf16_elect(tmem + e.z, ((uint64_t)kDescHi << 32) | e.x, ((uint64_t)kDescHi << 32) | (e.y + wlo),
+                                      e.w, 1u);
                 }
             }
             ptx::mma_commit_elect(&sh.bar_tile[iw]);
@@ -748,15 +771,65 @@ __device__ __forceinline__ void row_wait(uint32_t (&r)[C / 16][16]) {
 // padded position and its periodic image along y (the MMAs read the x images
 // from the columns themselves); or, after the last layer, the head
 // contributions of the position.
-template <int C>
+template <int C, bool F8 = false>
 __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *contrib, const float *bias,
                                         const float *wa, const float (&hb)[C == 16 ? C : 1], bool last, int x, int y,
-                                        int yimg, int g, const uint32_t (&r)[C / 16][16], int *err) {
+                                        int yimg, int g, const uint32_t (&r)[C / 16][16], int *err,
+                                        const float *scl = nullptr) {
     constexpr int KC = C / 8, HB = C == 16 ? C : 1;
     const int G = pl.G, L = pl.L, Lp = pl.Lp;
     float v[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c >> 4][c & 15]);
+    if constexpr (F8) {
+        if (!last) {
+            // e4m3 outputs (16 channels): SiLU(s v + b) with s the layer's weight scale of the channel (1 in
+            // layer 0), computed as z / 2 = (s / 2) v + b / 2; saturated to +-448, 16 bytes a row
+            uint32_t w[4];
+#pragma unroll
+            for (int c4 = 0; c4 < C; c4 += 4) {
+                const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(1.f, 1.f, 1.f, 1.f);
+                const float ss[4] = {s4.x, s4.y, s4.z, s4.w};
+                float o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float hz = fmaf(0.5f * ss[k], v[c4 + k], hb[(c4 + k) % HB]);
+                    o[k] = fmaf(hz, ptx::tanh_approx(hz), hz);
+                }
+                w[c4 / 4] = ptx::pack_e4m3(o[0], o[1]) | (ptx::pack_e4m3(o[2], o[3]) << 16);
+            }
+            const int xp = x + 1;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int yp = b == 0 ? y + 1 : yimg;
+                if (yp < 0) continue;
+                const uint32_t row = (uint32_t)((xp * Lp + yp) * G + g);
+                if (!NQS_INDEX_OK(row < (uint32_t)pl.rows_total, err)) continue;
+                ptx::st_shared_v4(act + row * 16u, w[0], w[1], w[2], w[3]);
+            }
+        } else {
+            float ca = 0.f, cp = 0.f;
+#pragma unroll
+            for (int c4 = 0; c4 < C; c4 += 4) {
+                const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
+                const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(1.f, 1.f, 1.f, 1.f);
+                const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
+                const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
+                const float bb[4] = {b.x, b.y, b.z, b.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w};
+                const float aa[4] = {xa.x, xa.y, xa.z, xa.w}, pp[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float hv = ptx::silu_fast(fmaf(ss[k], v[c4 + k], bb[k]));
+                    ca = fmaf(aa[k], hv, ca);
+                    cp = fmaf(pp[k], hv, cp);
+                }
+            }
+            const int idx = g * pl.N + y * L + x;
+            contrib[idx] = ca;
+            contrib[G * pl.N + idx] = cp;
+        }
+        return;
+    }
     if (!last) {
         uint32_t w[C / 2];
 #pragma unroll
@@ -805,12 +878,18 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
 // SiLU of each output and its bf16 rows (with periodic images) written back
 // into the activation buffer, or after the last layer the head contributions.
 // Each thread walks its columns with the next column's TMEM load in flight.
-template <int C>
+template <int C, bool F8 = false>
 __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, int l, int *err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = warp & 3;
     const bool last = l == pl.n_layers - 1;
     const int G = pl.G, L = pl.L;
     const float *bias = sh.f32 + l * C;
+    // e4m3 weight scales of layer l >= 1: after its image in the weight buffer it was loaded into (that buffer
+    // is refilled only at the next layer's issue, after this epilogue)
+    const uint32_t qw = st.wseq + (uint32_t)l;
+    const float *scl = F8 && l > 0 ? reinterpret_cast<const float *>(sh.base + ((qw & 1) ? pl.o_w1 : pl.o_w0) +
+                                                                      12 * C * C)
+                                   : nullptr;
     const float *wa = sh.f32 + pl.n_layers * C;
     const uint32_t act = row_act(pl, sh);
     float *contrib = reinterpret_cast<float *>(sh.base + pl.o_act);
@@ -841,12 +920,12 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
             for (int x = x0; x < x1; x += 2) {
                 const bool more = x + 1 < x1;
                 if (more) row_ld<C>(tmem + (uint32_t)((x + 1) * C), rb);
-                if (valid) row_out<C>(pl, act, contrib, bias, wa, hb, last, x, y, yimg, g, ra, err);
+                if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x, y, yimg, g, ra, err, scl);
                 if (!more) break;
                 row_wait<C>(rb);
                 const bool more2 = x + 2 < x1;
                 if (more2) row_ld<C>(tmem + (uint32_t)((x + 2) * C), ra);
-                if (valid) row_out<C>(pl, act, contrib, bias, wa, hb, last, x + 1, y, yimg, g, rb, err);
+                if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x + 1, y, yimg, g, rb, err, scl);
                 if (more2) row_wait<C>(ra);
             }
         }
@@ -861,13 +940,13 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
 
 // Evaluate the group's G configurations (sh.spins) in the row form; results
 // in sh.res. False if a wait timed out (the block must stop).
-template <int C>
+template <int C, bool F8 = false>
 __device__ bool row_forward(const TcPlan &pl, const TcShared &sh, const unsigned char *packed, TcState &st, int *err) {
     build_rows(pl, sh);
-    row_issue<C>(pl, sh, packed, st, 0, err);
+    row_issue<C, F8>(pl, sh, packed, st, 0, err);
     for (int l = 0; l < pl.n_layers; ++l) {
-        if (!row_epilogue<C>(pl, sh, st, l, err)) return false;
-        if (l + 1 < pl.n_layers) row_issue<C>(pl, sh, packed, st, l + 1, err);
+        if (!row_epilogue<C, F8>(pl, sh, st, l, err)) return false;
+        if (l + 1 < pl.n_layers) row_issue<C, F8>(pl, sh, packed, st, l + 1, err);
         else head_slot(pl, sh, 0, nullptr, reinterpret_cast<const float *>(sh.base + pl.o_act));
     }
     st.wseq += (uint32_t)pl.n_layers;
@@ -1060,7 +1139,7 @@ __global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>) logpsi_tc_kernel(Tc
 // E_loc = H_diag + sum_k H_k exp((a'_k - a) + i (phi'_k - phi)) in float64,
 // every term of the sample at once, fixed-order block reduction.
 // ROWS: the configurations go through the row form (no cones).
-template <int C, bool ROWS = false>
+template <int C, bool ROWS = false, bool F8 = false>
 __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &sh, TcState &st,
                             const unsigned char *packed, const int8_t *cfg, const double *logpsi_s, double *out_s,
                             int *err, unsigned char *cache) {
@@ -1163,7 +1242,7 @@ __device__ bool eloc_sample(const TcPlan &pl, const Problem &p, const TcShared &
             }
             __syncthreads();
             if (ROWS) {
-                if (!row_forward<C>(pl, sh, packed, st, err)) return false;
+                if (!row_forward<C, F8>(pl, sh, packed, st, err)) return false;
             } else if (!tc_forward<C>(pl, sh, packed, st, err, band, cache, (cone && lead && e0 == 0) ? cache : nullptr)) {
                 return false;
             }
@@ -1215,8 +1294,9 @@ __global__ void __launch_bounds__(kTcThreads, kMinBlocks<C>)
     tc_teardown(pl, sh, st);
 }
 
-// Local energies through the row form (plans with L * C <= 256 columns).
-template <int C>
+// Local energies through the row form (plans with L * C <= 256 columns);
+// F8: e4m3 operands in layers >= 1 (16 channels).
+template <int C, bool F8 = false>
 __global__ void __launch_bounds__(kTcThreads, 2)
     eloc_rows_kernel(TcPlan pl, Problem p, const unsigned char *packed, const int8_t *configs, const double *logpsi,
                      int64_t n, double *out, int *err) {
@@ -1226,8 +1306,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     tc_init(sh, smem, pl.tmem_cols, st);
     row_bind(pl, sh, packed, st);
     for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
-        if (!eloc_sample<C, true>(pl, p, sh, st, packed, configs + s * p.N, logpsi ? logpsi + 2 * s : nullptr,
-                                  out + 2 * s, err, nullptr))
+        if (!eloc_sample<C, true, F8>(pl, p, sh, st, packed, configs + s * p.N, logpsi ? logpsi + 2 * s : nullptr,
+                                      out + 2 * s, err, nullptr))
             break;
     tc_teardown(pl, sh, st);
 }
@@ -1507,15 +1587,47 @@ __global__ void tc_pack_kernel(Problem p, TcPlan pl, const double *params, unsig
         const int dyi = o / 3, j = 2 - o % 3;
         dr[(((dyi * (C / 8) + k / 8) * 3 + j) * C + n) * 8 + (k % 8)] = __float2bfloat16_rn((float)w);
     }
+    // e4m3 images of layers >= 1 (layer 0 keeps bf16 operands); the scale of output channel n is the largest
+    // |weight| of the channel over 448, the largest e4m3 value
+    if (pl.f8bytes == 0) return;
+    for (int e = tid; e < (p.n_layers - 1) * C; e += nth) {
+        const int l = 1 + e / C, n = e - (l - 1) * C;
+        const double *wn = params + layer_offset(p, l) + (size_t)n * C * 9;   // [cin][dy][dx] of channel n
+        double m = 0.0;
+        for (int k = 0; k < 9 * C; ++k) m = fmax(m, fabs(wn[k]));
+        const float sc = m > 0.0 ? (float)m / 448.f : 1.f;
+        // row-form image [pair q][K half h][column block j = 1 - dx][C][16 input channels]: kernel row
+        // dy = 2 q + h (dy = 3: zero), so one K = 32 operand holds two kernel rows; then the scales
+        unsigned char *dst = packed + pl.f32_bytes + pl.w0bytes + 2 * (size_t)(p.n_layers - 1) * pl.wbytes +
+                             (size_t)(l - 1) * pl.f8bytes;
+        reinterpret_cast<float *>(dst + 12 * C * C)[n] = sc;
+        for (int q = 0; q < 2; ++q)
+            for (int h = 0; h < 2; ++h)
+                for (int j = 0; j < 3; ++j) {
+                    const int dy = 2 * q + h, dxi = 2 - j;
+                    unsigned short *row = reinterpret_cast<unsigned short *>(dst + (((q * 2 + h) * 3 + j) * C + n) * 16);
+                    for (int k = 0; k < 16; k += 2) {
+                        const float w0 = dy < 3 ? (float)wn[k * 9 + dy * 3 + dxi] / sc : 0.f;
+                        const float w1 = dy < 3 ? (float)wn[(k + 1) * 9 + dy * 3 + dxi] / sc : 0.f;
+                        row[k / 2] = (unsigned short)ptx::pack_e4m3(w0, w1);
+                    }
+                }
+    }
 }
 
 // ---------------------------------------------------------------- host planning
+// Packed image: fp32 block (biases [n_layers][C], head [2][C]), bf16 layer 0,
+// bf16 tap-form and row-form images of layers >= 1, and with 16 channels the
+// e4m3 row-form images of layers >= 1, each followed by its fp32 weight
+// scales [C].
 void plan_weights(const Problem &p, TcPlan &pl) {
     pl.K0 = p.c_in == 1 ? 16 : 32;
     pl.f32_count = p.n_layers * p.C + 2 * p.C;
     pl.f32_bytes = al16(pl.f32_count * 4);
     pl.w0bytes = (uint32_t)pl.K0 * p.C * 2u;
     pl.wbytes = 9u * p.C * p.C * 2u;
+    pl.wstride = pl.wbytes;
+    pl.f8bytes = p.C == 16 ? 12u * p.C * p.C + 4u * p.C : 0u;   // [pair][K half][j][C][16], scales [C]
 }
 
 int eloc_extra(const Problem &p);
@@ -1740,7 +1852,8 @@ bool tc_supported(const Problem &p, std::string *why) {
 size_t tc_packed_bytes(const Problem &p) {
     TcPlan pl{};
     plan_weights(p, pl);
-    return pl.f32_bytes + pl.w0bytes + 2 * (size_t)(p.n_layers - 1) * pl.wbytes;   // tap and row images
+    // tap and row images, e4m3 row images
+    return pl.f32_bytes + pl.w0bytes + 2 * (size_t)(p.n_layers - 1) * pl.wbytes + (size_t)(p.n_layers - 1) * pl.f8bytes;
 }
 
 int launch_tc_pack(const Problem &p, const double *p64, void *packed, const LaunchEnv &env) {
@@ -1799,13 +1912,30 @@ size_t tc_eloc_cache_bytes(const Problem &p, size_t max_smem, int num_sms, int64
 
 int launch_eloc_tc(const Problem &p, const double *, const void *packed, const int8_t *configs,
                    const double *logpsi, int64_t n, double *out, void *cache, size_t cache_bytes,
-                   const LaunchEnv &env) {
+                   const LaunchEnv &env, bool f8) {
     if (n == 0) return NQS_OK;
     std::string why;
     TcPlan pl;
     if (!tc_supported(p, &why)) {
         *env.msg = why;
         return NQS_ERR_UNSUPPORTED;
+    }
+    if (f8) {
+        // e4m3 operands: the row form with 16 channels; the sample's log psi is always recomputed, so that
+        // every ratio of the local energy is taken in the same arithmetic
+        if (p.C != 16 || !use_row_form(p, env.max_smem, &pl)) {
+            *env.msg = "e4m3 local energies need the row form with 16 channels";
+            return NQS_ERR_UNSUPPORTED;
+        }
+        pl.f8 = 1;
+        pl.wimg = 2u * (uint32_t)(p.n_layers - 1) * pl.wbytes;
+        pl.wstride = pl.f8bytes;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * pl.ctas));
+        auto k = eloc_rows_kernel<16, true>;
+        if (int rc = prep(k, pl, env)) return rc;
+        k<<<grid, 32 * (pl.epi + kIssuers), pl.total, env.stream>>>(pl, p, (const unsigned char *)packed, configs,
+                                                                    nullptr, n, out, env.err);
+        return check(env, "eloc_rows_kernel (e4m3)");
     }
     if (use_row_form(p, env.max_smem, &pl)) {
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * pl.ctas));

@@ -126,6 +126,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);   // M >> 4
 }
 
+// Instruction descriptor for kind::f8f6f4 with e4m3 A and B (both K-major,
+// K = 32 per instruction), fp32 accumulator, dense, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4)                       // D format: f32
+           | (0u << 7)                     // A format: e4m3
+           | (0u << 10)                    // B format: e4m3
+           | ((uint32_t)(N >> 3) << 17)    // N >> 3
+           | ((uint32_t)(M >> 4) << 24);   // M >> 4
+}
+
 // D[tmem] (+)= A[smem] * B[smem]; accumulate = 0 overwrites D.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -148,6 +158,18 @@ __device__ __forceinline__ void mma_bf16_elect(uint32_t d_tmem, uint64_t adesc, 
         "setp.ne.b32 p, %4, 0;\n\t"
         "elect.sync _|e, 0xffffffff;\n\t"
         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// The same for e4m3 operands (kind::f8f6f4), issued by one elected lane.
+__device__ __forceinline__ void mma_e4m3_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -221,6 +243,14 @@ __device__ __forceinline__ float silu_fast(float z) {
 __device__ __forceinline__ float silu_bias(float v, float hb) {
     const float hz = fmaf(0.5f, v, hb);
     return fmaf(hz, tanh_approx(hz), hz);
+}
+
+// Two floats to e4m3 (round to nearest even, saturating to +-448), lo in the
+// low byte of the 16-bit result.
+__device__ __forceinline__ uint32_t pack_e4m3(float lo, float hi) {
+    unsigned short r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return (uint32_t)r;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

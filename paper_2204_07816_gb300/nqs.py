@@ -20,7 +20,7 @@ STATUS = {0: 'NQS_OK', -1: 'NQS_ERR_INVALID_ARG', -2: 'NQS_ERR_OOM', -3: 'NQS_ER
           -5: 'NQS_ERR_NOT_CONVERGED', -6: 'NQS_ERR_TIMEOUT', -7: 'NQS_ERR_UNSUPPORTED', -8: 'NQS_ERR_BOUNDS'}
 NQS_ERR_NOT_CONVERGED = -5
 NQS_ERR_UNSUPPORTED = -7
-PRECISION = {'fp64': 0, 'fp32': 1, 'bf16': 2}
+PRECISION = {'fp64': 0, 'fp32': 1, 'bf16': 2, 'fp8': 3}
 MODEL = {'j1j2': 0, 'tj': 1}
 
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
