@@ -923,6 +923,29 @@ def main():
     check = {'energy_per_site_vs_fp64_gpu': abs(e_this[:, 0].mean() - e_fp64[:, 0].mean()) / N,
              'max_abs_eloc_diff_vs_fp64_gpu': float(np.abs(e_this[:, 0] - e_fp64[:, 0]).max())}
 
+    # the FP8 form of the same local energies (row-form plans with 16 channels): the step's last samples, L2
+    # flushed before each launch, CUDA events on the context's stream
+    fp8 = None
+    if args.precision == 'bf16' and w['channels'] == 16 and nqs.tc_plan(prob, 'local_energy', n_samples)['row_form']:
+        ctx.local_energy(cfg_last, None, 'fp8')
+        torch.cuda.synchronize()
+        t8 = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a8, b8 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a8.record(stream)
+            e8 = ctx.local_energy(cfg_last, None, 'fp8')
+            b8.record(stream)
+            torch.cuda.synchronize()
+            t8.append(a8.elapsed_time(b8))
+        e8 = e8.cpu().numpy()
+        ms8 = float(np.mean(t8))
+        fp8 = {'eloc_ms': ms8, 'eloc_samples_per_s': n_samples / (ms8 / 1e3),
+               'energy_per_site_vs_fp64_gpu': abs(e8[:, 0].mean() - e_fp64[:, 0].mean()) / N,
+               'max_abs_eloc_diff_per_site_vs_fp64_gpu': float(np.abs(e8[:, 0] - e_fp64[:, 0]).max()) / N,
+               'what': 'layer 0 bf16, layers >= 1 e4m3 operands with per-output-channel weight scales, fp32 '
+                       'accumulation, float64 ratios and sums (eloc_rows_kernel, e4m3)'}
+
     # plain FP32 path on the same workload
     cmp = None
     if args.compare_steps > 0 and args.precision != 'fp32':
@@ -974,6 +997,16 @@ def main():
         e_sub = ctx.local_energy(cfg_last[:args.oracle_samples], None, args.precision).cpu().numpy()
         check['energy_per_site_vs_oracle_subset'] = abs(e_sub[:, 0].mean() - e_or.real.mean()) / N
         check['oracle_subset_samples'] = int(sub.shape[0])
+        if fp8 is not None:
+            fp8['energy_per_site_vs_oracle_subset'] = abs(e8[:sub.shape[0], 0].mean() - e_or.real.mean()) / N
+            peak8 = 2.0 * (peaks.get('bf16_tflops_sustained') or peaks['bf16_tflops'])
+            ach8 = flops / (ms8 / 1e3) / 1e12
+            fp8['roofline'] = {'bound': 'tensor', 'achieved': ach8, 'peak': peak8, 'unit': 'TFLOP/s',
+                               'frac': ach8 / peak8, 'kernel': 'eloc_rows_kernel (e4m3)',
+                               'peak_source': '%s bf16 dense (sustained) x 2, the nominal e4m3 / bf16 ratio' % peak_kind,
+                               'flops': 'cone form, as the main line',
+                               'dense_form': {'achieved': flops_dense / (ms8 / 1e3) / 1e12,
+                                              'frac': flops_dense / (ms8 / 1e3) / 1e12 / peak8}}
         line = {
             'metric': METRIC, 'value': value, 'unit': 'samples/s', 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': float(step_total_ms / args.steps), 'higher_is_better': True,
@@ -988,6 +1021,7 @@ def main():
             'energy_check': check,
             'roofline': roof,
             'roofline_sx': sx,
+            'fp8': fp8,
             'cpu_baseline': {'value': sub.shape[0] / dt_or, 'unit': 'samples/s', 'cores': cores, 'kind': 'oracle',
                              'sample': '%d of the step\'s samples, E_loc only (FP64 numpy oracle, spawn pool)' %
                                        sub.shape[0]},
