@@ -38,7 +38,8 @@ def parse():
     ap.add_argument('--steps', type=int, default=5)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32', 'fp64'])
+    ap.add_argument('--precision', default='bf16', choices=['bf16', 'fp32', 'fp64', 'fp8'],
+                    help='fp8 (local energies only) with --profile-eloc; the SR step reports its FP8 form under "fp8"')
     ap.add_argument('--workload', default='j1j2_10x10')
     ap.add_argument('--compare-steps', type=int, default=2, help='steps of the plain FP32 path')
     ap.add_argument('--oracle-samples', type=int, default=256, help='bounded sample for the CPU oracle')
@@ -62,7 +63,10 @@ def parse():
                          'of their chains, and against the same launches back to back')
     ap.add_argument('--serve-partition', action='store_true',
                     help='serving mode with per-class SM shares (default: every request sized for the whole GPU)')
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision == 'fp8' and not args.profile_eloc:
+        ap.error('--precision fp8 runs local energies only: use it with --profile-eloc')
+    return args
 
 
 def serve_mix(n_req, seed=0, mean_gap_s=0.3, steps=2, lattices=(6, 8, 10, 12, 16, 24, 36)):

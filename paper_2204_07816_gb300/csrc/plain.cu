@@ -18,7 +18,7 @@ __global__ void convert_params_kernel(const double *__restrict__ p64, float *__r
 }
 
 // ------------------------------------------------------------------ log psi
-template <typename T, int CB>
+template <typename T, int CB, bool PN>
 __global__ void __launch_bounds__(kThreads) logpsi_plain_kernel(Problem p, const T *params, const double *p64,
                                                                 const int8_t *configs, int64_t n, double *out,
                                                                 PlainLayout lay) {
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kThreads) logpsi_plain_kernel(Problem p, const
         const int gc = (int)std::min<int64_t>(G, n - b0);
         for (int r = threadIdx.x; r < gc * N; r += blockDim.x) spins[r] = configs[b0 * N + r];
         __syncthreads();
-        plain_forward<T, CB>(p, params, p64, spins, gc, net);
+        plain_forward<T, CB, PN>(p, params, p64, spins, gc, net);
         for (int g = threadIdx.x; g < gc; g += blockDim.x) {
             out[2 * (b0 + g)] = net.a[g];
             out[2 * (b0 + g) + 1] = net.phi[g];
@@ -60,7 +60,7 @@ __host__ __device__ inline ElocSmem eloc_smem(const Problem &p, size_t base, int
     return e;
 }
 
-template <typename T, int CB>
+template <typename T, int CB, bool PN>
 __global__ void __launch_bounds__(kThreads) eloc_plain_kernel(Problem p, const T *params, const double *p64,
                                                               const int8_t *configs, const double *logpsi,
                                                               int64_t n, double *out, PlainLayout lay, int *err) {
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) eloc_plain_kernel(Problem p, const T
                 spins[r] = (int8_t)v;
             }
             __syncthreads();
-            plain_forward<T, CB>(p, params, p64, spins, gc, net);
+            plain_forward<T, CB, PN>(p, params, p64, spins, gc, net);
             if (e0 == 0 && recompute && threadIdx.x == 0) { ref[0] = net.a[0]; ref[1] = net.phi[0]; }
             __syncthreads();
             for (int g = threadIdx.x; g < gc; g += blockDim.x) {
@@ -215,7 +215,7 @@ __device__ __forceinline__ int neighbour_dir(int i, int d, int L) {
     return site_at(x + dx, y + dy, L);
 }
 
-template <typename T, int CB>
+template <typename T, int CB, bool PN>
 __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const T *params, const double *p64,
                                                                 int8_t *chains, int n_chains, uint64_t step0,
                                                                 uint64_t seed, int spc, int sweeps_between,
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
     const int gc = min(G, n_chains - c0);
     for (int r = threadIdx.x; r < gc * N; r += blockDim.x) cur[r] = chains[(size_t)c0 * N + r];
     __syncthreads();
-    plain_forward<T, CB>(p, params, p64, cur, gc, net);
+    plain_forward<T, CB, PN>(p, params, p64, cur, gc, net);
     for (int g = threadIdx.x; g < gc; g += blockDim.x) { ca[g] = net.a[g]; cphi[g] = net.phi[g]; }
     if (threadIdx.x == 0) { scnt[0] = 0; scnt[1] = 0; }
     __syncthreads();
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) sample_plain_kernel(Problem p, const
                     spins[r] = cur[g * N + src];
                 }
                 __syncthreads();
-                plain_forward<T, CB>(p, params, p64, spins, cnt, net);
+                plain_forward<T, CB, PN>(p, params, p64, spins, cnt, net);
                 for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
                     const int g = list[m];
                     const double delta = 2.0 * (net.a[m] - ca[g]);
@@ -334,10 +334,10 @@ __device__ __forceinline__ void acc_out(double *acc, int k, T v) { acc[k] += (do
 // One sample. VJP = false: rows Oa, Op of O (two output-gradient streams).
 // VJP = true: one stream seeded with ga w_a + gp w_phi, the sample's vector
 // added to acc (each parameter by the same thread for every sample).
-template <typename T, bool VJP>
+template <typename T, bool VJP, bool PN>
 __device__ void grad_plain_sample(const Problem &p, const T *params, const double *p64, const int8_t *cfg, double *Oa,
                                   double *Op, double ga, double gp, double *acc, T *base, T *hbar) {
-    if (p.net != NQS_NET_SILU) {   // the paper's CNN1 / CNN2 (d phi = 0)
+    if constexpr (PN) {   // the paper's CNN1 / CNN2 (d phi = 0)
         paper_grad_sample<T, VJP>(p, params, cfg, Oa, Op, ga, acc, base);
         return;
     }
@@ -450,20 +450,20 @@ __device__ void grad_plain_sample(const Problem &p, const T *params, const doubl
     }
 }
 
-template <typename T>
+template <typename T, bool PN>
 __global__ void __launch_bounds__(kThreads) grad_plain_kernel(Problem p, const T *params, const double *p64,
                                                               const int8_t *configs, int64_t n, double *O,
                                                               T *scratch, size_t per_block) {
     __shared__ T hbar[64];
     T *base = scratch + per_block * blockIdx.x;
     for (int64_t s = blockIdx.x; s < n; s += gridDim.x)
-        grad_plain_sample<T, false>(p, params, p64, configs + s * p.N, O + (size_t)s * p.P, O + (size_t)(n + s) * p.P,
+        grad_plain_sample<T, false, PN>(p, params, p64, configs + s * p.N, O + (size_t)s * p.P, O + (size_t)(n + s) * p.P,
                                     0.0, 0.0, nullptr, base, hbar);
 }
 
 // Vector-Jacobian products summed per chunk of K consecutive samples (one
 // block per chunk, samples in order) into part[chunk][P].
-template <typename T>
+template <typename T, bool PN>
 __global__ void __launch_bounds__(kThreads) vjp_plain_kernel(Problem p, const T *params, const double *p64,
                                                              const int8_t *configs, int64_t n, const double *grad,
                                                              int64_t K, double *part, T *scratch, size_t per_block) {
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kThreads) vjp_plain_kernel(Problem p, const T 
         __syncthreads();
         const int64_t s1 = min(n, (q + 1) * K);
         for (int64_t s = q * K; s < s1; ++s)
-            grad_plain_sample<T, true>(p, params, p64, configs + s * p.N, nullptr, nullptr, grad[2 * s],
+            grad_plain_sample<T, true, PN>(p, params, p64, configs + s * p.N, nullptr, nullptr, grad[2 * s],
                                        grad[2 * s + 1], acc, base, hbar);
         __syncthreads();
     }
@@ -500,13 +500,21 @@ int plain_max_group(const Problem &p, int prec, size_t extra_smem, size_t max_sm
     return G;
 }
 
-#define NQS_DISPATCH_CB(C, ...)                                            \
-    switch (C) {                                                           \
-        case 4: { constexpr int CB = 4; __VA_ARGS__; } break;             \
-        case 8: { constexpr int CB = 8; __VA_ARGS__; } break;             \
-        case 16: { constexpr int CB = 16; __VA_ARGS__; } break;           \
-        case 32: { constexpr int CB = 16; __VA_ARGS__; } break;           \
-        default: return NQS_ERR_UNSUPPORTED;                               \
+// PN: the network family's instantiation; CB: channel block of the SiLU
+// convolutions (one instantiation serves the paper's families)
+#define NQS_DISPATCH_NET(P, ...)                                           \
+    if ((P).net != NQS_NET_SILU) { constexpr bool PN = true; __VA_ARGS__; } \
+    else { constexpr bool PN = false; __VA_ARGS__; }
+#define NQS_DISPATCH_CB(P, ...)                                            \
+    if ((P).C != 4 && (P).C != 8 && (P).C != 16 && (P).C != 32) return NQS_ERR_UNSUPPORTED; \
+    if ((P).net != NQS_NET_SILU) { constexpr bool PN = true; constexpr int CB = 4; __VA_ARGS__; } \
+    else {                                                                 \
+        constexpr bool PN = false;                                         \
+        switch ((P).C) {                                                   \
+            case 4: { constexpr int CB = 4; __VA_ARGS__; } break;         \
+            case 8: { constexpr int CB = 8; __VA_ARGS__; } break;         \
+            default: { constexpr int CB = 16; __VA_ARGS__; } break;       \
+        }                                                                  \
     }
 
 static int check_launch(const LaunchEnv &env, const char *what) {
@@ -537,8 +545,8 @@ static int logpsi_plain_t(const Problem &p, const T *params, const double *p64, 
     const size_t bytes = lay.total + align16((size_t)G * p.N);
     const int64_t groups = (n + G - 1) / G;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)env.num_sms * 4));
-    NQS_DISPATCH_CB(p.C, {
-        auto k = logpsi_plain_kernel<T, CB>;
+    NQS_DISPATCH_CB(p, {
+        auto k = logpsi_plain_kernel<T, CB, PN>;
         int rc = set_smem<T>(k, bytes, env);
         if (rc) return rc;
         k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, configs, n, out, lay);
@@ -561,8 +569,8 @@ static int eloc_plain_t(const Problem &p, const T *params, const double *p64, co
     const PlainLayout lay = plain_layout<T>(p, G);
     const size_t bytes = eloc_smem(p, lay.total, G).total;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)env.num_sms * 8));
-    NQS_DISPATCH_CB(p.C, {
-        auto k = eloc_plain_kernel<T, CB>;
+    NQS_DISPATCH_CB(p, {
+        auto k = eloc_plain_kernel<T, CB, PN>;
         int rc = set_smem<T>(k, bytes, env);
         if (rc) return rc;
         k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, configs, logpsi, n, out, lay, env.err);
@@ -605,8 +613,8 @@ static int sample_plain_t(const Problem &p, const T *params, const double *p64, 
     const PlainLayout lay = plain_layout<T>(p, G);
     const size_t bytes = sample_smem(p, lay.total, G).total;
     const int grid = (n_chains + G - 1) / G;
-    NQS_DISPATCH_CB(p.C, {
-        auto k = sample_plain_kernel<T, CB>;
+    NQS_DISPATCH_CB(p, {
+        auto k = sample_plain_kernel<T, CB, PN>;
         int rc = set_smem<T>(k, bytes, env);
         if (rc) return rc;
         k<<<grid, kThreads, bytes, env.stream>>>(p, params, p64, chains, n_chains, step0, seed, spc, sb, burn,
@@ -642,12 +650,14 @@ int launch_vjp_plain(const Problem &p, int prec, const DeviceParams &dp, const i
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>(nq, (int64_t)env.num_sms * 2),
                              (int64_t)(scratch_bytes / (grad_per_block(p) * esz))));
-    if (prec == NQS_FP64)
-        vjp_plain_kernel<double><<<blocks, kThreads, 0, env.stream>>>(p, dp.p64, dp.p64, configs, n, grad, K, part,
-                                                                      (double *)scratch, grad_per_block(p));
-    else
-        vjp_plain_kernel<float><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, grad, K, part,
-                                                                     (float *)scratch, grad_per_block(p));
+    NQS_DISPATCH_NET(p, {
+        if (prec == NQS_FP64)
+            vjp_plain_kernel<double, PN><<<blocks, kThreads, 0, env.stream>>>(p, dp.p64, dp.p64, configs, n, grad, K,
+                                                                              part, (double *)scratch, grad_per_block(p));
+        else
+            vjp_plain_kernel<float, PN><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, grad, K,
+                                                                             part, (float *)scratch, grad_per_block(p));
+    });
     return check_launch(env, "vjp_plain_kernel");
 }
 
@@ -656,12 +666,14 @@ int launch_grad_plain(const Problem &p, int prec, const DeviceParams &dp, const 
     if (n == 0) return NQS_OK;
     const size_t esz = prec == NQS_FP64 ? 8 : 4;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(scratch_bytes / (grad_per_block(p) * esz))));
-    if (prec == NQS_FP64)
-        grad_plain_kernel<double><<<blocks, kThreads, 0, env.stream>>>(p, dp.p64, dp.p64, configs, n, O,
-                                                                        (double *)scratch, grad_per_block(p));
-    else
-        grad_plain_kernel<float><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, O,
-                                                                       (float *)scratch, grad_per_block(p));
+    NQS_DISPATCH_NET(p, {
+        if (prec == NQS_FP64)
+            grad_plain_kernel<double, PN><<<blocks, kThreads, 0, env.stream>>>(p, dp.p64, dp.p64, configs, n, O,
+                                                                                (double *)scratch, grad_per_block(p));
+        else
+            grad_plain_kernel<float, PN><<<blocks, kThreads, 0, env.stream>>>(p, dp.p32, dp.p64, configs, n, O,
+                                                                               (float *)scratch, grad_per_block(p));
+    });
     return check_launch(env, "grad_plain_kernel");
 }
 
@@ -807,13 +819,15 @@ extern "C" int nqs_logpsi_grad_noalloc(const nqs_problem *q, const double *param
     const int64_t fit = (int64_t)(scratch_bytes / per_block);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(n, fit), (int64_t)num_sms * 2));
     if (f64) {
-        grad_plain_kernel<double><<<blocks, kThreads, 0, s>>>(p, params, params, configs, n, O_out,
-                                                               reinterpret_cast<double *>(scratch), grad_per_block(p));
+        NQS_DISPATCH_NET(p, grad_plain_kernel<double, PN><<<blocks, kThreads, 0, s>>>(
+                                p, params, params, configs, n, O_out, reinterpret_cast<double *>(scratch),
+                                grad_per_block(p)));
     } else {
         float *p32 = static_cast<float *>(base);
         convert_params_kernel<<<(p.P + 255) / 256, 256, 0, s>>>(params, p32, p.P);
-        grad_plain_kernel<float><<<blocks, kThreads, 0, s>>>(p, p32, params, configs, n, O_out,
-                                                              reinterpret_cast<float *>(scratch), grad_per_block(p));
+        NQS_DISPATCH_NET(p, grad_plain_kernel<float, PN><<<blocks, kThreads, 0, s>>>(
+                                p, p32, params, configs, n, O_out, reinterpret_cast<float *>(scratch),
+                                grad_per_block(p)));
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) { g_noalloc_error = std::string("launch: ") + cudaGetErrorString(e); return NQS_ERR_CUDA; }

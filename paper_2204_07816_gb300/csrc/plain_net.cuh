@@ -55,10 +55,14 @@ struct PlainNet {
 // (shared memory). params: layer weights in type T (flat layout);
 // params64: the float64 vector (head read in float64). Results in net.a,
 // net.phi. All threads of the block must call.
-template <typename T, int CB>
+// PN: the paper's CNN1 / CNN2 (p.net), a separate instantiation so that the
+// SiLU kernels carry none of its code (it cost them registers: measured
+// 1.6-2.3x slower FP32 local energies and sampling when the families shared
+// one kernel).
+template <typename T, int CB, bool PN = false>
 __device__ void plain_forward(const Problem &p, const T *__restrict__ params, const double *__restrict__ params64,
                               const int8_t *spins, int G, PlainNet<T> &net) {
-    if (p.net != NQS_NET_SILU) {   // the paper's CNN1 / CNN2
+    if constexpr (PN) {
         paper_forward<T>(p, params, spins, G, net.act0, net.act1, net.a, net.phi);
         return;
     }
