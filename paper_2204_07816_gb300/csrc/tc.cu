@@ -784,16 +784,17 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
     if constexpr (F8) {
         if (!last) {
             // e4m3 outputs (16 channels): SiLU(s v + b) with s the layer's weight scale of the channel (1 in
-            // layer 0), computed as z / 2 = (s / 2) v + b / 2; saturated to +-448, 16 bytes a row
+            // layer 0), computed as z / 2 = (s / 2) v + b / 2 from the halved scales; saturated to +-448, 16
+            // bytes a row
             uint32_t w[4];
 #pragma unroll
             for (int c4 = 0; c4 < C; c4 += 4) {
-                const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(1.f, 1.f, 1.f, 1.f);
+                const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(.5f, .5f, .5f, .5f);
                 const float ss[4] = {s4.x, s4.y, s4.z, s4.w};
                 float o[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float hz = fmaf(0.5f * ss[k], v[c4 + k], hb[(c4 + k) % HB]);
+                    const float hz = fmaf(ss[k], v[c4 + k], hb[(c4 + k) % HB]);
                     o[k] = fmaf(hz, ptx::tanh_approx(hz), hz);
                 }
                 w[c4 / 4] = ptx::pack_e4m3(o[0], o[1]) | (ptx::pack_e4m3(o[2], o[3]) << 16);
@@ -812,14 +813,16 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
 #pragma unroll
             for (int c4 = 0; c4 < C; c4 += 4) {
                 const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
-                const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(1.f, 1.f, 1.f, 1.f);
+                const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(.5f, .5f, .5f, .5f);
                 const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
                 const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
                 const float bb[4] = {b.x, b.y, b.z, b.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w};
                 const float aa[4] = {xa.x, xa.y, xa.z, xa.w}, pp[4] = {xq.x, xq.y, xq.z, xq.w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float hv = ptx::silu_fast(fmaf(ss[k], v[c4 + k], bb[k]));
+                    // z / 2 = (s / 2) v + b / 2, exactly half of s v + b
+                    const float hz = fmaf(ss[k], v[c4 + k], 0.5f * bb[k]);
+                    const float hv = fmaf(hz, ptx::tanh_approx(hz), hz);
                     ca = fmaf(aa[k], hv, ca);
                     cp = fmaf(pp[k], hv, cp);
                 }
@@ -884,7 +887,7 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
     const bool last = l == pl.n_layers - 1;
     const int G = pl.G, L = pl.L;
     const float *bias = sh.f32 + l * C;
-    // e4m3 weight scales of layer l >= 1: after its image in the weight buffer it was loaded into (that buffer
+    // halved e4m3 weight scales of layer l >= 1: after its image in the weight buffer it was loaded into (that buffer
     // is refilled only at the next layer's issue, after this epilogue)
     const uint32_t qw = st.wseq + (uint32_t)l;
     const float *scl = F8 && l > 0 ? reinterpret_cast<const float *>(sh.base + ((qw & 1) ? pl.o_w1 : pl.o_w0) +
@@ -1600,7 +1603,7 @@ __global__ void tc_pack_kernel(Problem p, TcPlan pl, const double *params, unsig
         // dy = 2 q + h (dy = 3: zero), so one K = 32 operand holds two kernel rows; then the scales
         unsigned char *dst = packed + pl.f32_bytes + pl.w0bytes + 2 * (size_t)(p.n_layers - 1) * pl.wbytes +
                              (size_t)(l - 1) * pl.f8bytes;
-        reinterpret_cast<float *>(dst + 12 * C * C)[n] = sc;
+        reinterpret_cast<float *>(dst + 12 * C * C)[n] = 0.5f * sc;   // halved, as the epilogue uses it
         for (int q = 0; q < 2; ++q)
             for (int h = 0; h < 2; ++h)
                 for (int j = 0; j < 3; ++j) {
@@ -1619,7 +1622,7 @@ __global__ void tc_pack_kernel(Problem p, TcPlan pl, const double *params, unsig
 // Packed image: fp32 block (biases [n_layers][C], head [2][C]), bf16 layer 0,
 // bf16 tap-form and row-form images of layers >= 1, and with 16 channels the
 // e4m3 row-form images of layers >= 1, each followed by its fp32 weight
-// scales [C].
+// scales [C], halved.
 void plan_weights(const Problem &p, TcPlan &pl) {
     pl.K0 = p.c_in == 1 ? 16 : 32;
     pl.f32_count = p.n_layers * p.C + 2 * p.C;

@@ -35,3 +35,28 @@ def test_local_energy_bf16_full_batch(name, n, rows, fp64_rows):
     half = n // 2
     e2 = torch.cat([ctx.local_energy(cfg[:half], None, 'bf16'), ctx.local_energy(cfg[half:], None, 'bf16')])
     assert torch.equal(e2, e)
+
+
+def test_local_energy_fp8_full_batch():
+    """The FP8 form at the 10x10 workload size in one launch over the whole
+    batch: sampled rows against the oracle (per-sample bound of the e4m3
+    form, 5e-3 per site), the batch energy per site against the FP64 GPU path
+    within the 1e-4 validity condition, and bitwise-equal rows when the batch
+    is split in two launches."""
+    w = WL['j1j2_10x10']
+    N = w['L'] ** 2
+    n = 8192
+    ctx, params = make_ctx(w, param_seed=91)
+    spec, ham = oracle_of(w)
+    cfg = dev(configs_for(w, n, seed=93))
+    e = ctx.local_energy(cfg, None, 'fp8')
+    e_h = e.cpu().numpy()
+    assert np.all(np.isfinite(e_h))
+    pick = np.unique(np.linspace(0, n - 1, 8).astype(int))
+    want = eloc.local_energy(params, cfg[pick].cpu().numpy(), spec, ham)
+    assert np.abs(e_h[pick, 0] - want.real).max() / N <= 5e-3
+    e64 = ctx.local_energy(cfg, None, 'fp64').cpu().numpy()
+    assert abs(e_h[:, 0].mean() - e64[:, 0].mean()) / N <= 1e-4
+    half = n // 2
+    e2 = torch.cat([ctx.local_energy(cfg[:half], None, 'fp8'), ctx.local_energy(cfg[half:], None, 'fp8')])
+    assert torch.equal(e2, e)
