@@ -300,6 +300,33 @@ def test_sampler_counts_bf16():
     assert m0 > 0 and a0 == m0
 
 
+def test_sampler_bf16_waves_of_chains():
+    """More chains than one wave of co-resident sampler blocks (one chain per
+    block, three blocks per SM: more than 456 chains on 152 SMs): every chain
+    still has its block, later waves start as blocks retire. A chain's path
+    depends only on its index and the seed, so the first 300 chains of a
+    1,200-chain run equal a 300-chain run bitwise (configurations and log psi),
+    and an SM share (fewer blocks, each taking several chains in turn) gives
+    the 1,200 chains bitwise too."""
+    w = WL['j1j2_10x10']
+    over = {'n_layers': 3}
+    from tests.gpu_common import problem_of
+    plan = lib().tc_plan(problem_of(w, **over), 'sample', 1200)
+    assert (plan['G'], plan['slots'], plan['grid']) == (1, 1, 1200)
+    ctx_a, _ = make_ctx(w, seed=9, **over)
+    cfg_a, lp_a = ctx_a.sample(1200, 2, 1, 2, 'bf16')
+    ctx_b, _ = make_ctx(w, seed=9, **over)
+    cfg_b, lp_b = ctx_b.sample(300, 2, 1, 2, 'bf16')
+    ctx_c, _ = make_ctx(w, seed=9, **over)
+    ctx_c.set_sm_limit(8)
+    cfg_c, lp_c = ctx_c.sample(1200, 2, 1, 2, 'bf16')
+    torch.cuda.synchronize()
+    assert torch.equal(cfg_a[:600], cfg_b) and torch.equal(lp_a[:600], lp_b)
+    assert torch.equal(cfg_a, cfg_c) and torch.equal(lp_a, lp_c)
+    # and the stored log psi is the bf16 log psi of the stored configuration
+    assert torch.equal(ctx_a.logpsi(cfg_a, 'bf16'), lp_a)
+
+
 def nqs_param_count_of(w, **over):
     from tests.gpu_common import problem_of
     return lib().nqs_param_count(problem_of(w, **over))
