@@ -957,6 +957,12 @@ def main():
         cmp = {'eloc_samples_per_s': n_samples * args.compare_steps / (st32[:, 1].sum() / 1000.0),
                'sr_steps_per_s': args.compare_steps / (st32.sum() / 1000.0),
                'ms_per_step': float(st32.sum(axis=1).mean()), 'eloc_ms': float(st32[:, 1].mean())}
+        # the baseline's own roofline: the same cone-form FLOPs against the FP32 CUDA-core peak at the clock seen
+        mhz32 = (clocks or {}).get('sm_mhz') or 2070.0
+        fp32_peak = 152 * 128 * 2 * mhz32 * 1e6 / 1e12
+        cmp['eloc_tflops'] = flops / (cmp['eloc_ms'] / 1e3) / 1e12
+        cmp['eloc_frac_of_fp32_cuda_core_peak'] = cmp['eloc_tflops'] / fp32_peak
+        cmp['fp32_cuda_core_peak_tflops'] = fp32_peak
         ctx32.close()
 
     line = None

@@ -71,6 +71,10 @@ def dev(a, dtype=None):
 
 
 def rel_err(a, b):
+    """Largest absolute difference over the batch divided by the largest
+    magnitude of the reference b over the batch: a per-batch relative bound
+    (an entry much smaller than the batch's largest is held to the same
+    absolute error, not to the bound relative to itself)."""
     a = np.asarray(a)
     b = np.asarray(b)
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)

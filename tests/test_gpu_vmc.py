@@ -47,7 +47,8 @@ def test_fp64_sr_steps_match_the_oracle_chain(sr_method):
         assert (r['moves'], r['accepted']) == (counts['moves'], counts['accepted'])
         assert abs(r['energy_per_site'] - em.real / 16) <= 1e-11 * abs(em.real / 16)
         assert abs(r['energy_imag_per_site'] - em.imag / 16) <= 1e-11
-        assert r['cg_converged'] and r['cg_residual'] <= 1e-10
+        # CG stops at rtol 1e-12; the sample-space solve's residual is the Cholesky's rounding, evaluated from O
+        assert r['cg_converged'] and r['cg_residual'] <= (1e-12 if r['sr_method'] == 'cg' else 1e-10)
         assert r['sr_method'] == sr_method or (sr_method == 'auto' and (k > 0 or r['sr_method'] == 'cg'))
         assert abs(r['variance_per_site2'] - e.real.var() / 256) <= 1e-9 * e.real.var() / 256
         p = sr.update(p, delta, lr)
