@@ -455,7 +455,12 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
             for (int c = 0; c < C / 2; ++c) {
                 const float h0 = C == 16 ? hb[(2 * c) % HB] : 0.5f * bias[2 * c];
                 const float h1 = C == 16 ? hb[(2 * c + 1) % HB] : 0.5f * bias[2 * c + 1];
-                w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
+                if constexpr (C == 16) {   // packed pairs (32 channels: scalar, fewer live registers)
+                    const float2 o = ptx::silu_bias2(make_float2(v[2 * c], v[2 * c + 1]), make_float2(h0, h1));
+                    w[c] = ptx::pack_bf16(o.x, o.y);
+                } else {
+                    w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
+                }
             }
             if (!NQS_INDEX_OK(((dst.x & 0xFFFFu) == kNone || (dst.x & 0xFFFFu) < (uint32_t)pl.rbuf) &&
                                   ((dst.x >> 16) == kNone || (dst.x >> 16) < (uint32_t)pl.rbuf) &&
@@ -482,11 +487,19 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
                 const float4 xp = *reinterpret_cast<const float4 *>(wa + C + c4);
                 const float bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {xa.x, xa.y, xa.z, xa.w};
                 const float pp[4] = {xp.x, xp.y, xp.z, xp.w};
+                float hv[4];
+                if constexpr (C == 16) {
+                    const float2 h01 = ptx::silu_fast2(make_float2(v[c4], v[c4 + 1]), make_float2(bb[0], bb[1]));
+                    const float2 h23 = ptx::silu_fast2(make_float2(v[c4 + 2], v[c4 + 3]), make_float2(bb[2], bb[3]));
+                    hv[0] = h01.x, hv[1] = h01.y, hv[2] = h23.x, hv[3] = h23.y;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) hv[k] = ptx::silu_fast(v[c4 + k] + bb[k]);
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float hv = ptx::silu_fast(v[c4 + k] + bb[k]);
-                    ca = fmaf(aa[k], hv, ca);
-                    cp = fmaf(pp[k], hv, cp);
+                    ca = fmaf(aa[k], hv[k], ca);
+                    cp = fmaf(pp[k], hv[k], cp);
                 }
             }
             // configuration-major in site order ([a | phi][g][y L + x]), so that the head reads one
@@ -791,13 +804,12 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
             for (int c4 = 0; c4 < C; c4 += 4) {
                 const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(.5f, .5f, .5f, .5f);
                 const float ss[4] = {s4.x, s4.y, s4.z, s4.w};
-                float o[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float hz = fmaf(ss[k], v[c4 + k], hb[(c4 + k) % HB]);
-                    o[k] = fmaf(hz, ptx::tanh_approx(hz), hz);
-                }
-                w[c4 / 4] = ptx::pack_e4m3(o[0], o[1]) | (ptx::pack_e4m3(o[2], o[3]) << 16);
+                const float2 o01 = ptx::silu_half2(__ffma2_rn(make_float2(ss[0], ss[1]), make_float2(v[c4], v[c4 + 1]),
+                                                              make_float2(hb[c4 % HB], hb[(c4 + 1) % HB])));
+                const float2 o23 = ptx::silu_half2(__ffma2_rn(make_float2(ss[2], ss[3]),
+                                                              make_float2(v[c4 + 2], v[c4 + 3]),
+                                                              make_float2(hb[(c4 + 2) % HB], hb[(c4 + 3) % HB])));
+                w[c4 / 4] = ptx::pack_e4m3(o01.x, o01.y) | (ptx::pack_e4m3(o23.x, o23.y) << 16);
             }
             const int xp = x + 1;
 #pragma unroll
@@ -818,13 +830,17 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
                 const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
                 const float bb[4] = {b.x, b.y, b.z, b.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w};
                 const float aa[4] = {xa.x, xa.y, xa.z, xa.w}, pp[4] = {xq.x, xq.y, xq.z, xq.w};
+                // z / 2 = (s / 2) v + b / 2, exactly half of s v + b
+                const float2 h01 = ptx::silu_half2(__ffma2_rn(make_float2(ss[0], ss[1]), make_float2(v[c4], v[c4 + 1]),
+                                                              make_float2(0.5f * bb[0], 0.5f * bb[1])));
+                const float2 h23 = ptx::silu_half2(__ffma2_rn(make_float2(ss[2], ss[3]),
+                                                              make_float2(v[c4 + 2], v[c4 + 3]),
+                                                              make_float2(0.5f * bb[2], 0.5f * bb[3])));
+                const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    // z / 2 = (s / 2) v + b / 2, exactly half of s v + b
-                    const float hz = fmaf(ss[k], v[c4 + k], 0.5f * bb[k]);
-                    const float hv = fmaf(hz, ptx::tanh_approx(hz), hz);
-                    ca = fmaf(aa[k], hv, ca);
-                    cp = fmaf(pp[k], hv, cp);
+                    ca = fmaf(aa[k], hv[k], ca);
+                    cp = fmaf(pp[k], hv[k], cp);
                 }
             }
             const int idx = g * pl.N + y * L + x;
@@ -839,7 +855,8 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
         for (int c = 0; c < C / 2; ++c) {
             const float h0 = C == 16 ? hb[(2 * c) % HB] : 0.5f * bias[2 * c];
             const float h1 = C == 16 ? hb[(2 * c + 1) % HB] : 0.5f * bias[2 * c + 1];
-            w[c] = ptx::pack_bf16(ptx::silu_bias(v[2 * c], h0), ptx::silu_bias(v[2 * c + 1], h1));
+            const float2 o = ptx::silu_bias2(make_float2(v[2 * c], v[2 * c + 1]), make_float2(h0, h1));
+            w[c] = ptx::pack_bf16(o.x, o.y);
         }
         const int xp = x + 1;
 #pragma unroll
@@ -863,11 +880,13 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
             const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
             const float bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {xa.x, xa.y, xa.z, xa.w};
             const float pp[4] = {xq.x, xq.y, xq.z, xq.w};
+            const float2 h01 = ptx::silu_fast2(make_float2(v[c4], v[c4 + 1]), make_float2(bb[0], bb[1]));
+            const float2 h23 = ptx::silu_fast2(make_float2(v[c4 + 2], v[c4 + 3]), make_float2(bb[2], bb[3]));
+            const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float hv = ptx::silu_fast(v[c4 + k] + bb[k]);
-                ca = fmaf(aa[k], hv, ca);
-                cp = fmaf(pp[k], hv, cp);
+                ca = fmaf(aa[k], hv[k], ca);
+                cp = fmaf(pp[k], hv[k], cp);
             }
         }
         // site order [a | phi][g][y * L + x]
@@ -911,24 +930,24 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
             const int y = valid ? m / G : 0, g = valid ? m - y * G : 0;
             const int yimg = y == 0 ? L + 1 : (y == L - 1 ? 0 : -1);
             const int nh = pl.epi >> 2, h = warp >> 2;
-            const int x0 = h * L / nh, x1 = (h + 1) * L / nh;
             float hb[C == 16 ? C : 1];
 #pragma unroll
             for (int c = 0; c < (C == 16 ? C : 1); ++c) hb[c] = 0.5f * bias[c];
             uint32_t ra[C / 16][16], rb[C / 16][16];
-            if (x0 < x1) {
-                row_ld<C>(tmem + (uint32_t)(x0 * C), ra);
+            // columns x = h, h + nh, ... (interleaved between the groups: measured faster than halves)
+            if (h < L) {
+                row_ld<C>(tmem + (uint32_t)(h * C), ra);
                 row_wait<C>(ra);
             }
-            for (int x = x0; x < x1; x += 2) {
-                const bool more = x + 1 < x1;
-                if (more) row_ld<C>(tmem + (uint32_t)((x + 1) * C), rb);
+            for (int x = h; x < L; x += 2 * nh) {
+                const bool more = x + nh < L;
+                if (more) row_ld<C>(tmem + (uint32_t)((x + nh) * C), rb);
                 if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x, y, yimg, g, ra, err, scl);
                 if (!more) break;
                 row_wait<C>(rb);
-                const bool more2 = x + 2 < x1;
-                if (more2) row_ld<C>(tmem + (uint32_t)((x + 2) * C), ra);
-                if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x + 1, y, yimg, g, rb, err, scl);
+                const bool more2 = x + 2 * nh < L;
+                if (more2) row_ld<C>(tmem + (uint32_t)((x + 2 * nh) * C), ra);
+                if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x + nh, y, yimg, g, rb, err, scl);
                 if (more2) row_wait<C>(ra);
             }
         }
