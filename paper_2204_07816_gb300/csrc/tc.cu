@@ -482,17 +482,20 @@ __device__ bool epilogue_layer(const TcPlan &pl, const TcShared &sh, TcState &st
             float ca = 0.f, cp = 0.f;
 #pragma unroll
             for (int c4 = 0; c4 < C; c4 += 4) {
-                const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
                 const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
                 const float4 xp = *reinterpret_cast<const float4 *>(wa + C + c4);
-                const float bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {xa.x, xa.y, xa.z, xa.w};
-                const float pp[4] = {xp.x, xp.y, xp.z, xp.w};
+                const float aa[4] = {xa.x, xa.y, xa.z, xa.w}, pp[4] = {xp.x, xp.y, xp.z, xp.w};
                 float hv[4];
                 if constexpr (C == 16) {
-                    const float2 h01 = ptx::silu_fast2(make_float2(v[c4], v[c4 + 1]), make_float2(bb[0], bb[1]));
-                    const float2 h23 = ptx::silu_fast2(make_float2(v[c4 + 2], v[c4 + 3]), make_float2(bb[2], bb[3]));
+                    // SiLU(v + b) from the halved biases held in registers: fma(0.5, v, b / 2) rounds to the
+                    // value 0.5 (v + b) rounds to (scaling by 2 is exact), so the result is that of silu_fast
+                    const float2 h01 = ptx::silu_bias2(make_float2(v[c4], v[c4 + 1]), make_float2(hb[c4], hb[c4 + 1]));
+                    const float2 h23 = ptx::silu_bias2(make_float2(v[c4 + 2], v[c4 + 3]),
+                                                       make_float2(hb[c4 + 2], hb[c4 + 3]));
                     hv[0] = h01.x, hv[1] = h01.y, hv[2] = h23.x, hv[3] = h23.y;
                 } else {
+                    const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
+                    const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) hv[k] = ptx::silu_fast(v[c4 + k] + bb[k]);
                 }
@@ -596,7 +599,7 @@ __device__ bool tc_forward(const TcPlan &pl, const TcShared &sh, const unsigned 
 // N = C) per x. All MMAs of a layer complete before its epilogue writes, so
 // one activation buffer is updated in place. The two issuing warps take the
 // left and right halves of the output columns (disjoint accumulators); the
-// epilogue warps take a TMEM lane quarter and half of the columns each.
+// epilogue warps take a TMEM lane quarter and every other column each.
 
 __device__ __forceinline__ uint32_t row_act(const TcPlan &pl, const TcShared &sh) {
     return ptx::smem_u32(sh.base + pl.o_act);
@@ -824,18 +827,17 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
             float ca = 0.f, cp = 0.f;
 #pragma unroll
             for (int c4 = 0; c4 < C; c4 += 4) {
-                const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
                 const float4 s4 = scl ? *reinterpret_cast<const float4 *>(scl + c4) : make_float4(.5f, .5f, .5f, .5f);
                 const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
                 const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
-                const float bb[4] = {b.x, b.y, b.z, b.w}, ss[4] = {s4.x, s4.y, s4.z, s4.w};
+                const float ss[4] = {s4.x, s4.y, s4.z, s4.w};
                 const float aa[4] = {xa.x, xa.y, xa.z, xa.w}, pp[4] = {xq.x, xq.y, xq.z, xq.w};
                 // z / 2 = (s / 2) v + b / 2, exactly half of s v + b
                 const float2 h01 = ptx::silu_half2(__ffma2_rn(make_float2(ss[0], ss[1]), make_float2(v[c4], v[c4 + 1]),
-                                                              make_float2(0.5f * bb[0], 0.5f * bb[1])));
+                                                              make_float2(hb[c4 % HB], hb[(c4 + 1) % HB])));
                 const float2 h23 = ptx::silu_half2(__ffma2_rn(make_float2(ss[2], ss[3]),
                                                               make_float2(v[c4 + 2], v[c4 + 3]),
-                                                              make_float2(0.5f * bb[2], 0.5f * bb[3])));
+                                                              make_float2(hb[(c4 + 2) % HB], hb[(c4 + 3) % HB])));
                 const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -875,13 +877,18 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
         float ca = 0.f, cp = 0.f;
 #pragma unroll
         for (int c4 = 0; c4 < C; c4 += 4) {
-            const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
             const float4 xa = *reinterpret_cast<const float4 *>(wa + c4);
             const float4 xq = *reinterpret_cast<const float4 *>(wa + C + c4);
-            const float bb[4] = {b.x, b.y, b.z, b.w}, aa[4] = {xa.x, xa.y, xa.z, xa.w};
-            const float pp[4] = {xq.x, xq.y, xq.z, xq.w};
-            const float2 h01 = ptx::silu_fast2(make_float2(v[c4], v[c4 + 1]), make_float2(bb[0], bb[1]));
-            const float2 h23 = ptx::silu_fast2(make_float2(v[c4 + 2], v[c4 + 3]), make_float2(bb[2], bb[3]));
+            const float aa[4] = {xa.x, xa.y, xa.z, xa.w}, pp[4] = {xq.x, xq.y, xq.z, xq.w};
+            float2 h01, h23;
+            if constexpr (C == 16) {   // the halved biases in registers (the same values, as in the tap form)
+                h01 = ptx::silu_bias2(make_float2(v[c4], v[c4 + 1]), make_float2(hb[c4], hb[c4 + 1]));
+                h23 = ptx::silu_bias2(make_float2(v[c4 + 2], v[c4 + 3]), make_float2(hb[c4 + 2], hb[c4 + 3]));
+            } else {
+                const float4 b = *reinterpret_cast<const float4 *>(bias + c4);
+                h01 = ptx::silu_fast2(make_float2(v[c4], v[c4 + 1]), make_float2(b.x, b.y));
+                h23 = ptx::silu_fast2(make_float2(v[c4 + 2], v[c4 + 3]), make_float2(b.z, b.w));
+            }
             const float hv[4] = {h01.x, h01.y, h23.x, h23.y};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
