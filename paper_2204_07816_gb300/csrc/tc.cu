@@ -786,12 +786,14 @@ __device__ __forceinline__ void row_wait(uint32_t (&r)[C / 16][16]) {
 // One output column x of one row (y, g): bias + SiLU to bf16, stored at the
 // padded position and its periodic image along y (the MMAs read the x images
 // from the columns themselves); or, after the last layer, the head
-// contributions of the position.
+// contributions of the position. The bf16 stores go to amain (the row's
+// address at padded column 0) plus the column's offset, and dimg bytes
+// further for the image; the e4m3 stores address act by row index.
 template <int C, bool F8 = false>
-__device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *contrib, const float *bias,
-                                        const float *wa, const float (&hb)[C == 16 ? C : 1], bool last, int x, int y,
-                                        int yimg, int g, const uint32_t (&r)[C / 16][16], int *err,
-                                        const float *scl = nullptr) {
+__device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, uint32_t amain, int dimg, float *contrib,
+                                        const float *bias, const float *wa, const float (&hb)[C == 16 ? C : 1],
+                                        bool last, int x, int y, int yimg, int g, const uint32_t (&r)[C / 16][16],
+                                        int *err, const float *scl = nullptr) {
     constexpr int KC = C / 8, HB = C == 16 ? C : 1;
     const int G = pl.G, L = pl.L, Lp = pl.Lp;
     float v[C];
@@ -814,6 +816,7 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
                                                               make_float2(hb[(c4 + 2) % HB], hb[(c4 + 3) % HB])));
                 w[c4 / 4] = ptx::pack_e4m3(o01.x, o01.y) | (ptx::pack_e4m3(o23.x, o23.y) << 16);
             }
+            // row addresses from the row index (measured faster here than the precomputed form below)
             const int xp = x + 1;
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
@@ -861,16 +864,17 @@ __device__ __forceinline__ void row_out(const TcPlan &pl, uint32_t act, float *c
             w[c] = ptx::pack_bf16(o.x, o.y);
         }
         const int xp = x + 1;
+        const uint32_t a = amain + (uint32_t)(xp * Lp * G) * 16u;   // row (xp Lp + y + 1) G + g
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int yp = b == 0 ? y + 1 : yimg;
             if (yp < 0) continue;
-            const uint32_t row = (uint32_t)((xp * Lp + yp) * G + g);
-            if (!NQS_INDEX_OK(row < (uint32_t)pl.rows_total, err)) continue;
+            if (!NQS_INDEX_OK((uint32_t)((xp * Lp + yp) * G + g) < (uint32_t)pl.rows_total, err)) continue;
+            const uint32_t ab = a + (b == 0 ? 0u : (uint32_t)dimg);
 #pragma unroll
             for (int kc = 0; kc < KC; ++kc)
-                ptx::st_shared_v4(act + (uint32_t)kc * pl.plane + row * 16u, w[4 * kc], w[4 * kc + 1],
-                                  w[4 * kc + 2], w[4 * kc + 3]);
+                ptx::st_shared_v4(ab + (uint32_t)kc * pl.plane, w[4 * kc], w[4 * kc + 1], w[4 * kc + 2],
+                                  w[4 * kc + 3]);
         }
     } else {
         // the tap form's head arithmetic: c = 0 .. C - 1 in order, 16-byte broadcast loads
@@ -936,6 +940,9 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
             const bool valid = m < G * L;
             const int y = valid ? m / G : 0, g = valid ? m - y * G : 0;
             const int yimg = y == 0 ? L + 1 : (y == L - 1 ? 0 : -1);
+            // this row's store address at padded column 0 and the byte offset of its periodic image along y
+            const uint32_t amain = act + (uint32_t)((y + 1) * G + g) * 16u;
+            const int dimg = (yimg - (y + 1)) * G * 16;
             const int nh = pl.epi >> 2, h = warp >> 2;
             float hb[C == 16 ? C : 1];
 #pragma unroll
@@ -949,12 +956,13 @@ __device__ bool row_epilogue(const TcPlan &pl, const TcShared &sh, TcState &st, 
             for (int x = h; x < L; x += 2 * nh) {
                 const bool more = x + nh < L;
                 if (more) row_ld<C>(tmem + (uint32_t)((x + nh) * C), rb);
-                if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x, y, yimg, g, ra, err, scl);
+                if (valid) row_out<C, F8>(pl, act, amain, dimg, contrib, bias, wa, hb, last, x, y, yimg, g, ra, err, scl);
                 if (!more) break;
                 row_wait<C>(rb);
                 const bool more2 = x + 2 * nh < L;
                 if (more2) row_ld<C>(tmem + (uint32_t)((x + 2 * nh) * C), ra);
-                if (valid) row_out<C, F8>(pl, act, contrib, bias, wa, hb, last, x + nh, y, yimg, g, rb, err, scl);
+                if (valid) row_out<C, F8>(pl, act, amain, dimg, contrib, bias, wa, hb, last, x + nh, y, yimg, g, rb,
+                                          err, scl);
                 if (more2) row_wait<C>(ra);
             }
         }
