@@ -367,18 +367,30 @@ def sx_iteration(ctx, O, e, iters=(4, 12)):
     return (times[1] - times[0]) / (iters[1] - iters[0])
 
 
-def sx_roofline(n_samples, P, iter_ms, peaks):
-    """Roofline entry of the S x products: algorithmic bytes 2 passes x 2 n_samples x P x 8 and FP64 FLOP
-    4 x 2 n_samples x P per CG iteration, against the measured copy bandwidth and the nominal FP64 rate."""
-    bytes_it = 2.0 * 2 * n_samples * P * 8
+def float_exact(O):
+    """True when every element of the float64 O is a float (the float32 and bf16 local derivatives are): the CG
+    then reads only the float plane of its split of O, 4 bytes an element."""
+    import torch
+    return bool((O.to(torch.float32).to(torch.float64) == O).all().item())
+
+
+def sx_roofline(n_samples, P, iter_ms, peaks, narrow):
+    """Roofline entry of the S x products: algorithmic bytes per CG iteration = 2 passes x 2 n_samples x P x the
+    bytes the passes read an element (4 from the float plane when O is made of floats, else 8 from the two planes),
+    against the measured copy bandwidth. The passes multiply-add in double-float arithmetic on the float32 pipes;
+    the float64 FLOP rate they stand in for (4 x 2 n_samples x P per iteration) is reported beside the nominal FP64
+    rate that a float64 FMA per element would be bound by."""
+    bpe = 4 if narrow else 8
+    bytes_it = 2.0 * 2 * n_samples * P * bpe
     flop_it = 4.0 * 2 * n_samples * P
     gbs = bytes_it / (iter_ms / 1e3) / 1e9
     tfs = flop_it / (iter_ms / 1e3) / 1e12
-    return {'kernels': 'gemv_rows_kernel + gemv_cols_kernel (+ P-vector kernels)', 'ms_per_cg_iteration': iter_ms,
+    return {'kernels': 'gemv_rows_df_kernel + gemv_cols_df_kernel (+ P-vector kernels)', 'ms_per_cg_iteration': iter_ms,
+            'planes': 'float plane only (O made of floats)' if narrow else 'float and low planes',
             'bytes_per_iteration': bytes_it, 'flop_per_iteration': flop_it,
             'hbm': {'achieved': gbs, 'peak': peaks['hbm_gbs'], 'unit': 'GB/s', 'frac': gbs / peaks['hbm_gbs']},
-            'fp64': {'achieved': tfs, 'peak': 1.25, 'unit': 'TFLOP/s', 'frac': tfs / 1.25,
-                     'peak_source': 'nominal FP64 rate of GB300'}}
+            'fp64_equivalent': {'achieved': tfs, 'nominal_fp64_peak': 1.25, 'unit': 'TFLOP/s',
+                                'what': 'float64 multiply-adds done in double-float on the FP32 pipes'}}
 
 
 def profile_sr(args):
@@ -513,7 +525,7 @@ def extra_workloads(args, peaks, uuid, pool, cores):
         'cg_iters': [int(i['iters']) for i in infos],
         'eloc_samples_per_s': w['n_samples'] / (eloc_ms / 1e3),
         'roofline_eloc': tc_roofline(w, ctx, cfg, eloc_ms),
-        'sx': sx_roofline(w['n_samples'], P, it_ms, peaks),
+        'sx': sx_roofline(w['n_samples'], P, it_ms, peaks, float_exact(O)),
         'energy_per_site_vs_fp64_gpu': abs(e16[:, 0].mean() - e64[:, 0].mean()) / w['L'] ** 2,
         'fp64_check_samples': int(sub.shape[0])}
     del O
@@ -1000,7 +1012,9 @@ def main():
                     'dense_form': {'achieved': flops_dense / eloc_launch_s / 1e12,
                                    'frac': flops_dense / eloc_launch_s / 1e12 / peak}}
         # S x products of the main workload: one CG iteration timed alone
-        sx = sx_roofline(n_samples, P, sx_iteration(ctx, ctx.logpsi_grad(cfg_last, args.precision), e_last), peaks)
+        O_last = ctx.logpsi_grad(cfg_last, args.precision)
+        sx = sx_roofline(n_samples, P, sx_iteration(ctx, O_last, e_last), peaks, float_exact(O_last))
+        del O_last
         # CPU oracle on a bounded sample of the same workload
         sub = cfg_last[:args.oracle_samples].cpu().numpy()
         e_or, dt_or = oracle_eloc(args.workload, params_at_step(ctx), sub, pool, cores)

@@ -22,7 +22,7 @@ namespace nqs {
 namespace {
 
 // scalar slots in the workspace
-enum : int { S_ERE = 0, S_EIM, S_RS, S_FNORM, S_DONE, S_ITER, S_MEANRE, S_MEANIM, S_WBRES, S_COUNT = 16 };
+enum : int { S_ERE = 0, S_EIM, S_RS, S_FNORM, S_DONE, S_ITER, S_MEANRE, S_MEANIM, S_WBRES, S_WIDE, S_COUNT = 16 };
 // P-vector kernels of a CG iteration run on ceil(P / kPvThreads) blocks (a grid that depends on P only, so the
 // partial sums and their fixed-order reduction do not depend on the device)
 constexpr int kPvThreads = 256;
@@ -35,6 +35,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// A float64 as a double-float h + l (the S.x passes below read vectors in this form).
+__device__ __forceinline__ float2 df_of(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
 }
 
 // Block-wide fixed-order sum (blockDim.x == kVecThreads).
@@ -71,6 +77,7 @@ __global__ void __launch_bounds__(kVecThreads) energy_kernel(const double *eloc,
         sc[S_EIM] = ei;
         sc[S_DONE] = 0.0;
         sc[S_ITER] = 0.0;
+        sc[S_WIDE] = 0.0;
     }
 }
 
@@ -94,6 +101,273 @@ __global__ void __launch_bounds__(kRowWarps * 32) gemv_rows_kernel(const double 
     for (; k < P; k += 32) a0 = fma(row[k], v[k], a0);
     const double s = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) y[r] = s;
+}
+
+// ---------------------------------------------------------------- double-float S.x passes
+// GB300 runs float64 FMAs at 1/64 of its float32 rate, and one float64 FMA
+// per element of O kept the FP64 pipe 82-86 % busy in the passes above while
+// HBM ran at half its bandwidth. The conjugate gradient therefore splits O
+// once per solve, in the pass that computes the force, into double-floats
+// (each element the unevaluated sum h + l of two floats, stored as a plane of
+// h and a plane of l), and its S.x passes multiply-add in double-float
+// arithmetic on the float32 pipes; float64 returns only for the row or column
+// totals. Products keep about 46 bits (the split truncates at 2^-46 of the
+// element, the l * l term is dropped) and every accumulation is a
+// renormalised double-float add, so a dot product's error stays near 1e-15 of
+// the sum of its terms' magnitudes (float64: about 1e-17). Where every
+// element of O is a float (the float32 and bf16 local derivatives are), the l
+// plane is all zero: the split pass records whether any l is not, and the
+// passes then read the h plane alone, half the bytes, with the same results.
+
+// a + b, both double-floats: two-sum of the high parts, then renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    const float u = __fadd_rn(t, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, u);
+    return make_float2(h, __fsub_rn(u, __fsub_rn(h, s)));
+}
+
+// acc + (ah + al) q for q = q.x + q.y: the exact product of the high parts (its
+// rounding error by one FMA) plus the two cross terms.
+__device__ __forceinline__ float2 df_fma(float ah, float al, float2 q, float2 acc) {
+    const float p = __fmul_rn(ah, q.x);
+    float e = fmaf(ah, q.x, -p);
+    e = fmaf(ah, q.y, e);
+    e = fmaf(al, q.x, e);
+    return df_add(acc, make_float2(p, e));
+}
+
+__device__ __forceinline__ double df_value(float2 a) { return (double)a.x + (double)a.y; }
+
+// A float64 (its two 32-bit words, w.x low, w.y high) as h + l by integer
+// operations, which leave the FP64 pipe to the force's FMAs in the same pass:
+// h carries the sign, the exponent rebiased and the top 23 mantissa bits, l
+// the next 23 bits (bits 28 .. 6 of the low word) as an integer float times
+// +-2^(E - 1069); |a - h - l| < 2^-46 |a|, and l = 0 exactly when a is a
+// float (its low 29 mantissa bits are zero). |a| < 2^-80 (zero, subnormals:
+// nothing an entry of O could add to a sum of O(1) terms) gives 0;
+// |a| >= 2^128, Inf and NaN give NaN.
+__device__ __forceinline__ float2 df_split_bits(uint2 w) {
+    const uint32_t sgn = w.y & 0x80000000u, t = w.y & 0x7FFFFFFFu;
+    const float h = __uint_as_float((((t - (896u << 20)) << 3) | (w.x >> 29)) | sgn);
+    const float m = __fsub_rn(__uint_as_float(0x4B000000u | ((w.x >> 6) & 0x7FFFFFu)), 8388608.f);
+    const float l = __fmul_rn(m, __uint_as_float((((t - (942u << 20)) >> 20) << 23) | sgn));
+    const bool tiny = t < (943u << 20), huge = t >= (1151u << 20);
+    return huge ? make_float2(__int_as_float(0x7FC00000), 0.f) : (tiny ? make_float2(0.f, 0.f) : make_float2(h, l));
+}
+
+// The force pass: zpart[chunk][k] = sum over the chunk's rows r of O[r, k] y[r]
+// in float64, in gemv_cols_kernel's order (the same sums), and every element
+// of O split into the planes Oh and Ol (row stride Pp = P rounded up to a
+// multiple of 4, the pad columns zero); sc[S_WIDE] = 1 if any l is not zero.
+__global__ void __launch_bounds__(kColThreads) gemv_cols_split_kernel(const double *__restrict__ O,
+                                                                      const double *__restrict__ y, int64_t rows, int P,
+                                                                      int Pp, int64_t chunk_rows,
+                                                                      double *__restrict__ zpart,
+                                                                      float *__restrict__ Oh, float *__restrict__ Ol,
+                                                                      double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    const int k = blockIdx.x * kColThreads + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * chunk_rows;
+    const int64_t r1 = rows < r0 + chunk_rows ? rows : r0 + chunk_rows;
+    bool wide = false;
+    if (k < P) {
+        const uint2 *col = reinterpret_cast<const uint2 *>(O) + k;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t r = r0;
+        for (; r + 3 < r1; r += 4) {
+            uint2 w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = __ldcs(col + (r + u) * P);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 d = df_split_bits(w[u]);
+                __stcs(Oh + (r + u) * Pp + k, d.x);
+                __stcs(Ol + (r + u) * Pp + k, d.y);
+                wide |= d.y != 0.f;
+            }
+            a0 = fma(__hiloint2double((int)w[0].y, (int)w[0].x), y[r], a0);
+            a1 = fma(__hiloint2double((int)w[1].y, (int)w[1].x), y[r + 1], a1);
+            a2 = fma(__hiloint2double((int)w[2].y, (int)w[2].x), y[r + 2], a2);
+            a3 = fma(__hiloint2double((int)w[3].y, (int)w[3].x), y[r + 3], a3);
+        }
+        for (; r < r1; ++r) {
+            const uint2 w = __ldcs(col + r * P);
+            const float2 d = df_split_bits(w);
+            __stcs(Oh + r * Pp + k, d.x);
+            __stcs(Ol + r * Pp + k, d.y);
+            wide |= d.y != 0.f;
+            a0 = fma(__hiloint2double((int)w.y, (int)w.x), y[r], a0);
+        }
+        zpart[(int64_t)blockIdx.y * P + k] = (a0 + a1) + (a2 + a3);
+    } else if (k < Pp) {
+        for (int64_t r = r0; r < r1; ++r) { Oh[r * Pp + k] = 0.f; Ol[r * Pp + k] = 0.f; }
+    }
+    // the same value from every writer
+    if (__any_sync(0xffffffffu, wide) && (threadIdx.x & 31) == 0) sc[S_WIDE] = 1.0;
+}
+
+// acc[j] += x[j] q[j] for the four columns of a float4 group (l parts zero
+// unless W).
+template <bool W>
+__device__ __forceinline__ void df_fma4(float2 (&acc)[4], float4 h, float4 l, float2 q0, float2 q1, float2 q2,
+                                        float2 q3) {
+    acc[0] = df_fma(h.x, W ? l.x : 0.f, q0, acc[0]);
+    acc[1] = df_fma(h.y, W ? l.y : 0.f, q1, acc[1]);
+    acc[2] = df_fma(h.z, W ? l.z : 0.f, q2, acc[2]);
+    acc[3] = df_fma(h.w, W ? l.w : 0.f, q3, acc[3]);
+}
+
+// y[r] = O[r, :] . v from the planes (one warp per row; lane i takes the float4
+// column groups i, i + 32, ...; accumulator j the j-th column of each group;
+// W: read the l plane too). The next U groups of each lane are loaded before
+// the current ones are consumed, so a warp keeps its loads in flight while it
+// computes. v holds Pp double-floats (zero past P). The order of every sum
+// does not depend on W or U, so a zero l plane gives the same y either way.
+template <bool W, int U>
+__device__ __forceinline__ void rows_df(const float *__restrict__ Oh, const float *__restrict__ Ol,
+                                        const float2 *__restrict__ v, int64_t r, int Pp, double *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int n4 = Pp >> 2;
+    const float4 *rh = reinterpret_cast<const float4 *>(Oh + r * (int64_t)Pp);
+    const float4 *rl = reinterpret_cast<const float4 *>(Ol + r * (int64_t)Pp);
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);   // two double-floats each
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 acc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] = make_float2(0.f, 0.f);
+    int c = lane;
+    float4 oh[U], ol[U];
+    if (c + 32 * (U - 1) < n4) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            oh[u] = __ldcs(rh + c + 32 * u);
+            ol[u] = W ? __ldcs(rl + c + 32 * u) : zero4;
+        }
+    }
+    while (c + 32 * (U - 1) < n4) {
+        const int cn = c + 32 * U;
+        const bool more = cn + 32 * (U - 1) < n4;
+        float4 nh[U], nl[U];
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                nh[u] = __ldcs(rh + cn + 32 * u);
+                nl[u] = W ? __ldcs(rl + cn + 32 * u) : zero4;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float4 qa = v4[2 * (c + 32 * u)], qb = v4[2 * (c + 32 * u) + 1];
+            df_fma4<W>(acc, oh[u], ol[u], make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y),
+                       make_float2(qb.z, qb.w));
+        }
+        c = cn;
+        if (!more) break;
+#pragma unroll
+        for (int u = 0; u < U; ++u) { oh[u] = nh[u]; ol[u] = nl[u]; }
+    }
+    for (; c < n4; c += 32) {
+        const float4 qa = v4[2 * c], qb = v4[2 * c + 1];
+        df_fma4<W>(acc, __ldcs(rh + c), W ? __ldcs(rl + c) : zero4, make_float2(qa.x, qa.y), make_float2(qa.z, qa.w),
+                   make_float2(qb.x, qb.y), make_float2(qb.z, qb.w));
+    }
+    const double s = warp_sum(df_value(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]))));
+    if (lane == 0) y[r] = s;
+}
+
+// ... and the block's partial sums of y over its real rows (r < n) and its
+// imaginary rows, in row order, into ypart[2 blockIdx.x + half].
+__global__ void __launch_bounds__(kRowWarps * 32) gemv_rows_df_kernel(const float *__restrict__ Oh,
+                                                                      const float *__restrict__ Ol,
+                                                                      const float2 *__restrict__ v, int64_t rows,
+                                                                      int Pp, double *__restrict__ y,
+                                                                      double *__restrict__ ypart, const double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    const int64_t r0 = (int64_t)blockIdx.x * kRowWarps;
+    const int64_t r = r0 + (threadIdx.x >> 5);
+    if (r < rows) {
+        if (sc[S_WIDE] != 0.0) rows_df<true, 2>(Oh, Ol, v, r, Pp, y);
+        else rows_df<false, 2>(Oh, Ol, v, r, Pp, y);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int64_t n = rows / 2;
+        double h0 = 0.0, h1 = 0.0;
+        for (int64_t q = r0; q < r0 + kRowWarps && q < rows; ++q) (q < n ? h0 : h1) += y[q];
+        ypart[2 * blockIdx.x] = h0;
+        ypart[2 * blockIdx.x + 1] = h1;
+    }
+}
+
+// zpart[chunk][k] = sum over the chunk's rows r of O[r, k] y[r] from the
+// planes, for the four columns k = 4 c4 ... 4 c4 + 3 of one thread (one
+// accumulator each, rows in order; the next U rows are loaded before the
+// current ones are consumed); W: read the l plane too.
+template <bool W, int U>
+__device__ __forceinline__ void cols_df(const float *__restrict__ Oh, const float *__restrict__ Ol,
+                                        const float2 *__restrict__ y, int64_t rows, int P, int Pp,
+                                        int64_t chunk_rows, int c4, double *__restrict__ zpart) {
+    const int64_t r0 = (int64_t)blockIdx.y * chunk_rows;
+    const int64_t r1 = rows < r0 + chunk_rows ? rows : r0 + chunk_rows;
+    const int64_t s4 = Pp >> 2;   // row stride in float4
+    const float4 *ch = reinterpret_cast<const float4 *>(Oh) + c4;
+    const float4 *cl = reinterpret_cast<const float4 *>(Ol) + c4;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 acc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] = make_float2(0.f, 0.f);
+    int64_t r = r0;
+    float4 oh[U], ol[U];
+    if (r + U - 1 < r1) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            oh[u] = __ldcs(ch + (r + u) * s4);
+            ol[u] = W ? __ldcs(cl + (r + u) * s4) : zero4;
+        }
+    }
+    while (r + U - 1 < r1) {
+        const int64_t rn = r + U;
+        const bool more = rn + U - 1 < r1;
+        float4 nh[U], nl[U];
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                nh[u] = __ldcs(ch + (rn + u) * s4);
+                nl[u] = W ? __ldcs(cl + (rn + u) * s4) : zero4;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float2 q = y[r + u];
+            df_fma4<W>(acc, oh[u], ol[u], q, q, q, q);
+        }
+        r = rn;
+        if (!more) break;
+#pragma unroll
+        for (int u = 0; u < U; ++u) { oh[u] = nh[u]; ol[u] = nl[u]; }
+    }
+    for (; r < r1; ++r) {
+        const float2 q = y[r];
+        df_fma4<W>(acc, __ldcs(ch + r * s4), W ? __ldcs(cl + r * s4) : zero4, q, q, q, q);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (4 * c4 + j < P) zpart[(int64_t)blockIdx.y * P + 4 * c4 + j] = df_value(acc[j]);
+}
+
+__global__ void __launch_bounds__(kColThreads) gemv_cols_df_kernel(const float *__restrict__ Oh,
+                                                                   const float *__restrict__ Ol,
+                                                                   const float2 *__restrict__ y, int64_t rows, int P,
+                                                                   int Pp, int64_t chunk_rows,
+                                                                   double *__restrict__ zpart, const double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    const int c4 = blockIdx.x * kColThreads + threadIdx.x;
+    if (c4 >= (Pp >> 2)) return;
+    if (sc[S_WIDE] != 0.0) cols_df<true, 4>(Oh, Ol, y, rows, P, Pp, chunk_rows, c4, zpart);
+    else cols_df<false, 16>(Oh, Ol, y, rows, P, Pp, chunk_rows, c4, zpart);
 }
 
 // Subtract the mean of each half of y (real rows, imaginary rows).
@@ -154,6 +428,25 @@ __device__ double pv_partials(const double *part, int nb, double *sh) {
     return pv_block_sum(v, sh);
 }
 
+// y minus the mean of each half (the means from the row pass's nb block
+// partials, summed in a fixed order by every block), and the result as
+// double-floats into yf; one element per thread.
+__global__ void __launch_bounds__(kPvThreads) center_df_kernel(double *y, int64_t n, const double *ypart, int nb,
+                                                                float2 *yf, const double *sc) {
+    if (sc[S_DONE] != 0.0) return;
+    __shared__ double sh[33];
+    double pr = 0.0, pi = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) { pr += ypart[2 * b]; pi += ypart[2 * b + 1]; }
+    const double mr = pv_block_sum(pr, sh) / (double)n;
+    const double mi = pv_block_sum(pi, sh) / (double)n;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < 2 * n) {
+        const double a = y[q] - (q < n ? mr : mi);
+        y[q] = a;
+        yf[q] = df_of(a);
+    }
+}
+
 // CG step, part 1: Ap = sum_chunks zpart / n + eps p; block partials of p . Ap.
 __global__ void __launch_bounds__(kPvThreads) cg_ap_kernel(const double *zpart, int nchunks, int P, int64_t n,
                                                             double eps, const double *p, double *Ap, double *part,
@@ -192,14 +485,18 @@ __global__ void __launch_bounds__(kPvThreads) cg_xr_kernel(int P, const double *
     if (threadIdx.x == 0) part2[blockIdx.x] = rn;
 }
 
-// Part 3: beta = (r . r) / rs; p = r + beta p.
+// Part 3: beta = (r . r) / rs; p = r + beta p (also as double-floats into pf).
 __global__ void __launch_bounds__(kPvThreads) cg_dir_kernel(int P, const double *r, double *p, const double *part2,
-                                                             const double *sc) {
+                                                             const double *sc, float2 *pf) {
     if (sc[S_DONE] != 0.0) return;
     __shared__ double sh[33];
     const double beta = pv_partials(part2, gridDim.x, sh) / sc[S_RS];
     const int k = blockIdx.x * kPvThreads + threadIdx.x;
-    if (k < P) p[k] = fma(beta, p[k], r[k]);
+    if (k < P) {
+        const double v = fma(beta, p[k], r[k]);
+        p[k] = v;
+        pf[k] = df_of(v);
+    }
 }
 
 // Part 4 (one block): iteration count, rs = r . r, convergence.
@@ -217,8 +514,10 @@ __global__ void __launch_bounds__(kPvThreads) cg_scalars_kernel(int nb, double r
 }
 
 // CG start: F = sum_chunks zpart / n; x = 0; r = p = F; block partials of |F|^2.
+// pf (nullable) receives p as double-floats.
 __global__ void __launch_bounds__(kPvThreads) cg_init_kernel(const double *zpart, int nchunks, int P, int64_t n,
-                                                              double *x, double *r, double *p, double *part) {
+                                                              double *x, double *r, double *p, double *part,
+                                                              float2 *pf) {
     __shared__ double sh[33];
     const int k = blockIdx.x * kPvThreads + threadIdx.x;
     double acc = 0.0;
@@ -229,7 +528,10 @@ __global__ void __launch_bounds__(kPvThreads) cg_init_kernel(const double *zpart
         x[k] = 0.0;
         r[k] = f;
         p[k] = f;
+        if (pf) pf[k] = df_of(f);
         acc = f * f;
+    } else if (pf && k < ((P + 3) & ~3)) {
+        pf[k] = make_float2(0.f, 0.f);   // the pad the vectorised row pass reads up to the plane stride
     }
     acc = pv_block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
@@ -496,18 +798,27 @@ __global__ void update_kernel(double *params, const double *x, int P, double lr)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) params[k] -= lr * x[k];
 }
 
-int chunks_for(int64_t rows, int P, int num_sms) {
-    const int col_blocks = (P + kColThreads - 1) / kColThreads;
+// Row chunks of a column pass with col_blocks blocks across the columns: about
+// eight blocks per SM, at least 64 rows a chunk, at most 256 chunks.
+int chunks_for_blocks(int64_t rows, int col_blocks, int num_sms) {
     int64_t want = std::max<int64_t>(1, (int64_t)num_sms * 8 / col_blocks);
     want = std::min<int64_t>(want, std::max<int64_t>(1, rows / 64));
     return (int)std::min<int64_t>(want, 256);
 }
 
+int chunks_for(int64_t rows, int P, int num_sms) {
+    return chunks_for_blocks(rows, (P + kColThreads - 1) / kColThreads, num_sms);
+}
+
 }  // namespace
 
 size_t sr_workspace_doubles(int64_t n, int P) {
-    // y [2n], Ap, r, p [P], zpart [256][P] upper bound, scalars, two block-partial arrays
-    return 2 * (size_t)n + 3 * (size_t)P + 256 * (size_t)P + S_COUNT + 2 * (size_t)((P + kPvThreads - 1) / kPvThreads);
+    // y [2n], Ap, r, p [P], zpart [256][P] upper bound, scalars, two block-partial arrays, then the double-float
+    // copies of p [Pp] and y [2n] and O's two float planes [2n][Pp] (Pp = P rounded up to a multiple of 4; one
+    // double's room per double-float) from a 16-byte boundary, the row pass's partial sums [2 ceil(2n / 8)]
+    const size_t Pp = (size_t)((P + 3) & ~3);
+    return 2 * (size_t)n + 3 * (size_t)P + 256 * (size_t)P + S_COUNT + 2 * (size_t)((P + kPvThreads - 1) / kPvThreads) +
+           1 + Pp + 2 * (size_t)n + 2 * (size_t)n * Pp + 2 * (size_t)((2 * n + kRowWarps - 1) / kRowWarps);
 }
 
 int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t n, double eps, double rtol,
@@ -526,13 +837,27 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     const int pvb = (P + kPvThreads - 1) / kPvThreads;
     double *part = sc + S_COUNT;
     double *part2 = part + pvb;
+    // double-float copies of p [Pp] and y [2n], then O as planes of h and of l [2n][Pp] each (written by the
+    // force pass), from a 16-byte boundary for the float4 loads
+    const int Pp = (P + 3) & ~3;
+    float2 *pf = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(part2 + pvb) + 15) & ~(uintptr_t)15);
+    float2 *yf = pf + Pp;
+    float *Oh = reinterpret_cast<float *>(yf + 2 * n);
+    float *Ol = Oh + (size_t)rows * Pp;
+    double *ypart = reinterpret_cast<double *>(Ol + (size_t)rows * Pp);   // [rgrid][2]
     cudaStream_t s = env.stream;
     const dim3 cgrid((P + kColThreads - 1) / kColThreads, nchunks);
     const int rgrid = (int)((rows + kRowWarps - 1) / kRowWarps);
+    const int cgb = (int)((rows + kPvThreads - 1) / kPvThreads);
+    // the double-float column pass: four columns a thread
+    const int dcb = (Pp / 4 + kColThreads - 1) / kColThreads;
+    const int nch_df = chunks_for_blocks(rows, dcb, env.num_sms);
+    const int64_t chunk_df = (rows + nch_df - 1) / nch_df;
+    const dim3 dgrid(dcb, nch_df);
 
     energy_kernel<<<1, kVecThreads, 0, s>>>(eloc, n, y, sc);
-    gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
-    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, part);
+    gemv_cols_split_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, Pp, chunk_rows, zpart, Oh, Ol, sc);
+    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, part, pf);
     cg_init_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
     if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR setup launch failed"; return NQS_ERR_CUDA; }
     *env.launches += 4;
@@ -545,12 +870,12 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     int batch = iters_out && *iters_out > 0 ? std::min(std::max(*iters_out + 2, 4), 64) : 4;
     while (max_iter > 0) {
         for (int b = 0; b < batch; ++b) {
-            gemv_rows_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(O, p, rows, P, y, sc);
-            center_kernel<<<1, kVecThreads, 0, s>>>(y, n, sc);
-            gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
-            cg_ap_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, eps, p, Ap, part, sc);
+            gemv_rows_df_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(Oh, Ol, pf, rows, Pp, y, ypart, sc);
+            center_df_kernel<<<cgb, kPvThreads, 0, s>>>(y, n, ypart, rgrid, yf, sc);
+            gemv_cols_df_kernel<<<dgrid, kColThreads, 0, s>>>(Oh, Ol, yf, rows, P, Pp, chunk_df, zpart, sc);
+            cg_ap_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch_df, P, n, eps, p, Ap, part, sc);
             cg_xr_kernel<<<pvb, kPvThreads, 0, s>>>(P, p, Ap, delta, r, part, part2, sc);
-            cg_dir_kernel<<<pvb, kPvThreads, 0, s>>>(P, r, p, part2, sc);
+            cg_dir_kernel<<<pvb, kPvThreads, 0, s>>>(P, r, p, part2, sc, pf);
             cg_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, rtol, max_iter, part2, sc);
         }
         done_iters += batch;
@@ -698,7 +1023,7 @@ int run_sr_woodbury(const Problem &pr, const double *O, const double *eloc, int6
     }
     // residual of the parameter-space system: |(S + eps I) delta - F| / |F|
     gemv_cols_kernel<<<dim3(colb, nch), kColThreads, 0, s>>>(O, ehat, m, P, chunk_rows, zpart, sc);
-    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch, P, n, tmp1, F, tmp2, part);
+    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch, P, n, tmp1, F, tmp2, part, nullptr);
     cg_init_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
     // (S_DONE is set when F = 0; delta is then 0 and the kernels below skip)
     gemv_rows_kernel<<<(unsigned)((m + kRowWarps - 1) / kRowWarps), kRowWarps * 32, 0, s>>>(O, delta, m, P, t, sc);

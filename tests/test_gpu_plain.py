@@ -256,8 +256,9 @@ def test_sr_solve_matches_oracle():
     assert abs(info['energy'] - em) <= 1e-12 * abs(em)
     d_cg, it, _, _ = sr.cg(dA, dPhi, e, 1e-4, 1e-8, 10000)
     _, info8 = ctx.sr_solve(O, E, eps=1e-4, rtol=1e-8)
-    # CG iteration counts drift with the summation order near the tolerance
-    assert abs(info8['iters'] - it) <= max(3, it // 10)
+    # CG iteration counts drift with the rounding near the tolerance: the float64 oracle's dot products against
+    # the CUDA path's double-float S.x products (about 46-bit products, errors near 1e-15 of the terms' sum)
+    assert abs(info8['iters'] - it) <= max(5, it // 5)
 
 
 def test_sr_update_applied_in_place():

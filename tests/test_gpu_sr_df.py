@@ -1,0 +1,83 @@
+"""The conjugate gradient's S.x products in double-float arithmetic (Sec. 3.2,
+the SR solve): the split of O into a plane of float high parts and a plane of
+float low parts, the narrow passes that read the high plane alone when O is
+made of floats (the float32 and bf16 local derivatives are), and the padded
+plane stride when P is not a multiple of 4, each against the oracle's dense
+solve of the same system in float64."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sr
+from tests.gpu_common import WL, dev, lib, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _system(P, n, seed, as_float):
+    rng = np.random.default_rng(seed)
+    dA = rng.normal(size=(n, P)) * np.exp(rng.normal(0.0, 1.0, size=P)) + rng.normal(size=P)
+    dPhi = 0.5 * rng.normal(size=(n, P))
+    e = -20.0 + rng.normal(size=n) + 0.3j * rng.normal(size=n)
+    if as_float:
+        dA = dA.astype(np.float32).astype(np.float64)
+        dPhi = dPhi.astype(np.float32).astype(np.float64)
+    return dA, dPhi, e
+
+
+def _ctx(net, channels):
+    """A context whose parameter count is the network's (CNN1 has P = 1 mod 4,
+    the SiLU family P = 0 mod 4); sr_solve reads no parameter values."""
+    nqs = lib()
+    prob = nqs.make_problem('j1j2', 4, n_layers=2, channels=channels, net=net)
+    P = nqs.nqs_param_count(prob)
+    params = torch.tensor(np.random.default_rng(5).normal(size=P) * 0.1, dtype=torch.float64, device='cuda')
+    return nqs.Context(prob, params, seed=0)
+
+
+NETS = [('silu', 4), ('silu', 8), ('cnn1', 4), ('cnn1', 8)]
+
+
+@pytest.mark.parametrize('net,channels', NETS)
+@pytest.mark.parametrize('as_float', [True, False])
+def test_cg_matches_dense_solve_float_planes(net, channels, as_float):
+    """Float-exact O (the float plane alone) and full float64 O (both planes);
+    P = 0 and 1 mod 4 (plane rows padded by 0 and 3 columns)."""
+    ctx = _ctx(net, channels)
+    P, n = ctx.P, 300
+    dA, dPhi, e = _system(P, n, 40 + channels + len(net), as_float)
+    O = dev(np.concatenate([dA, dPhi], 0))
+    E = dev(np.stack([e.real, e.imag], 1))
+    want, em = sr.solve_dense(dA, dPhi, e, 1e-3)
+    got, info = ctx.sr_solve(O, E, eps=1e-3, rtol=1e-12, max_iter=10000)
+    assert info['converged'] and info['resid'] <= 1e-12
+    assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-9 * np.linalg.norm(want)
+    assert abs(info['energy'] - em) <= 1e-12 * abs(em)
+    ctx.close()
+
+
+def test_plane_stride_residues_covered():
+    residues = set()
+    for net, channels in NETS:
+        ctx = _ctx(net, channels)
+        residues.add(ctx.P % 4)
+        ctx.close()
+    assert residues == {0, 1}, residues
+
+
+def test_float_planes_at_bench_size():
+    """8,192 samples of the 10x10 network's parameter count (P = 11,792), O made
+    of floats as the bf16 local derivatives are: the narrow passes at the size
+    the bench times, against the oracle's sample-space solve."""
+    w = WL['j1j2_10x10']
+    ctx, _ = make_ctx(w)
+    P, n = ctx.P, 2048
+    dA, dPhi, e = _system(P, n, 91, True)
+    O = dev(np.concatenate([dA, dPhi], 0))
+    E = dev(np.stack([e.real, e.imag], 1))
+    want, em = sr.solve_woodbury(dA, dPhi, e, 1e-4)
+    got, info = ctx.sr_solve(O, E, eps=1e-4, rtol=1e-11, max_iter=10000)
+    assert info['converged'] and info['resid'] <= 1e-11
+    assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-8 * np.linalg.norm(want)
+    ctx.close()
