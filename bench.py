@@ -1014,6 +1014,13 @@ def main():
         # S x products of the main workload: one CG iteration timed alone
         O_last = ctx.logpsi_grad(cfg_last, args.precision)
         sx = sx_roofline(n_samples, P, sx_iteration(ctx, O_last, e_last), peaks, float_exact(O_last))
+        # the same iteration with the float64 passes (nqs_set_sx_arithmetic NQS_SX_FP64), for comparison
+        ctx.set_sx_arithmetic('fp64')
+        ms64 = sx_iteration(ctx, O_last, e_last)
+        ctx.set_sx_arithmetic('double_float')
+        sx['fp64_passes'] = {'ms_per_cg_iteration': ms64,
+                             'fp64_tflops': 4.0 * 2 * n_samples * P / (ms64 / 1e3) / 1e12,
+                             'fp64_frac_of_nominal': 4.0 * 2 * n_samples * P / (ms64 / 1e3) / 1e12 / 1.25}
         del O_last
         # CPU oracle on a bounded sample of the same workload
         sub = cfg_last[:args.oracle_samples].cpu().numpy()

@@ -322,6 +322,24 @@ int nqs_logpsi_grad_noalloc(const nqs_problem *p, const double *params, const in
                             double *O_out, int32_t precision, void *stream);
 const char *nqs_noalloc_last_error(void);
 
+/* Arithmetic of the S.x products inside nqs_sr_solve's conjugate gradient.
+ * NQS_SX_DOUBLE_FLOAT (the default): the pass that computes the force also
+ * splits every float64 element of O into a float high part and a float low
+ * part (|error| < 2^-46 of the element; exact when the element is a float,
+ * as the NQS_FP32 and NQS_BF16 derivatives are), and each iteration's two
+ * passes over O multiply-add in double-float arithmetic (pairs of floats,
+ * renormalised sums, about 1e-15 of the sum of the terms' magnitudes) on the
+ * float32 pipes, reading only the high plane when every low part is zero.
+ * The force, every vector and scalar of the iteration and every row or
+ * column total stay float64. Needs 8 bytes per element of O more working
+ * memory (the two planes). NQS_SX_FP64: both passes in float64 FMAs on the
+ * float64 O itself (GB300's float64 FMA rate bounds them). */
+typedef enum { NQS_SX_DOUBLE_FLOAT = 0, NQS_SX_FP64 = 1 } nqs_sx_arithmetic;
+
+/* Select the S.x arithmetic of ctx's later nqs_sr_solve calls. Returns
+ * NQS_OK, or NQS_ERR_INVALID_ARG for another mode. */
+int nqs_set_sx_arithmetic(nqs_ctx *ctx, int32_t mode);
+
 /* Stochastic reconfiguration (Sec. 3.2; Sec. 5.4.1 "Distributed SR
  * computation", solved here matrix-free by conjugate gradient):
  *   <E> = mean E_loc, Oc = O - mean O,

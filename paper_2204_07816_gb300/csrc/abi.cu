@@ -45,6 +45,7 @@ struct nqs_ctx {
     size_t scratch_bytes = 0;
     int64_t launches = 0;
     int cg_hint = 0;               // iterations of the last CG solve (sizes the next solve's first launch batch)
+    int sx_arith = NQS_SX_DOUBLE_FLOAT;   // arithmetic of the CG's S.x passes
     void *multi_table = nullptr;   // request table of grouped launches led by this context
     size_t multi_table_bytes = 0;
     std::string msg;
@@ -531,7 +532,8 @@ int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, dou
     if (int rc = check_ctx(c)) return rc;
     if (n <= 0 || !O || !eloc || !delta) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve: bad arrays");
     if (!(eps >= 0.0) || !(rtol >= 0.0) || max_iter < 0) return fail(c, NQS_ERR_INVALID_ARG, "nqs_sr_solve: bad eps/rtol/max_iter");
-    if (int rc = ensure_scratch(c, sr_workspace_doubles(n, c->p.P) * sizeof(double))) return rc;
+    const int sx_fp64 = c->sx_arith == NQS_SX_FP64;
+    if (int rc = ensure_scratch(c, sr_workspace_doubles(n, c->p.P, sx_fp64) * sizeof(double))) return rc;
     LaunchEnv env = env_of(c);
     // the CG's partial sums are split by the device's SM count, not by an SM
     // limit, so the solve's rounding does not depend on the share a context
@@ -540,12 +542,20 @@ int nqs_sr_solve(nqs_ctx *c, const double *O, const double *eloc, int64_t n, dou
     int iters = c->cg_hint;
     double resid = 0.0, energy[2] = {0.0, 0.0};
     const int rc = run_sr_solve(c->p, O, eloc, n, eps, rtol, max_iter, lr, delta, c->params, apply_update,
-                                (double *)c->scratch, &iters, &resid, energy, env);
+                                (double *)c->scratch, &iters, &resid, energy, sx_fp64, env);
     if (rc == NQS_OK || rc == NQS_ERR_NOT_CONVERGED) c->cg_hint = iters;
     if (iters_out) *iters_out = iters;
     if (resid_out) *resid_out = resid;
     if (energy_out) { energy_out[0] = energy[0]; energy_out[1] = energy[1]; }
     return rc;
+}
+
+int nqs_set_sx_arithmetic(nqs_ctx *c, int32_t mode) {
+    if (int rc = check_ctx(c)) return rc;
+    if (mode != NQS_SX_DOUBLE_FLOAT && mode != NQS_SX_FP64)
+        return fail(c, NQS_ERR_INVALID_ARG, "nqs_set_sx_arithmetic: unknown mode");
+    c->sx_arith = mode;
+    return NQS_OK;
 }
 
 int nqs_sr_solve_woodbury(nqs_ctx *c, const double *O, const double *eloc, int64_t n, double eps, double lr,

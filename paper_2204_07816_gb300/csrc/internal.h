@@ -123,10 +123,10 @@ struct SrWorkspace {
     double *buf;
     size_t doubles;
 };
-size_t sr_workspace_doubles(int64_t n, int P);
+size_t sr_workspace_doubles(int64_t n, int P, int sx_fp64);
 int run_sr_solve(const Problem &p, const double *O, const double *eloc, int64_t n, double eps, double rtol,
                  int max_iter, double lr, double *delta, double *params, int apply, double *workspace,
-                 int *iters_out, double *resid_out, double *energy_out, const LaunchEnv &env);
+                 int *iters_out, double *resid_out, double *energy_out, int sx_fp64, const LaunchEnv &env);
 // sample-space (Woodbury) form: 2n x 2n Cholesky in place of CG
 size_t sr_woodbury_workspace_doubles(int64_t n, int P);
 int run_sr_woodbury(const Problem &p, const double *O, const double *eloc, int64_t n, double eps, double lr,

@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kPvThreads) cg_xr_kernel(int P, const double *
     if (threadIdx.x == 0) part2[blockIdx.x] = rn;
 }
 
-// Part 3: beta = (r . r) / rs; p = r + beta p (also as double-floats into pf).
+// Part 3: beta = (r . r) / rs; p = r + beta p (also as double-floats into pf, if not null).
 __global__ void __launch_bounds__(kPvThreads) cg_dir_kernel(int P, const double *r, double *p, const double *part2,
                                                              const double *sc, float2 *pf) {
     if (sc[S_DONE] != 0.0) return;
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kPvThreads) cg_dir_kernel(int P, const double 
     if (k < P) {
         const double v = fma(beta, p[k], r[k]);
         p[k] = v;
-        pf[k] = df_of(v);
+        if (pf) pf[k] = df_of(v);
     }
 }
 
@@ -812,18 +812,21 @@ int chunks_for(int64_t rows, int P, int num_sms) {
 
 }  // namespace
 
-size_t sr_workspace_doubles(int64_t n, int P) {
+size_t sr_workspace_doubles(int64_t n, int P, int sx_fp64) {
     // y [2n], Ap, r, p [P], zpart [256][P] upper bound, scalars, two block-partial arrays, then the double-float
     // copies of p [Pp] and y [2n] and O's two float planes [2n][Pp] (Pp = P rounded up to a multiple of 4; one
     // double's room per double-float) from a 16-byte boundary, the row pass's partial sums [2 ceil(2n / 8)]
+    // (the float64 passes need none of the double-float part)
     const size_t Pp = (size_t)((P + 3) & ~3);
-    return 2 * (size_t)n + 3 * (size_t)P + 256 * (size_t)P + S_COUNT + 2 * (size_t)((P + kPvThreads - 1) / kPvThreads) +
-           1 + Pp + 2 * (size_t)n + 2 * (size_t)n * Pp + 2 * (size_t)((2 * n + kRowWarps - 1) / kRowWarps);
+    const size_t base = 2 * (size_t)n + 3 * (size_t)P + 256 * (size_t)P + S_COUNT +
+                        2 * (size_t)((P + kPvThreads - 1) / kPvThreads);
+    if (sx_fp64) return base;
+    return base + 1 + Pp + 2 * (size_t)n + 2 * (size_t)n * Pp + 2 * (size_t)((2 * n + kRowWarps - 1) / kRowWarps);
 }
 
 int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t n, double eps, double rtol,
                  int max_iter, double lr, double *delta, double *params, int apply, double *ws, int *iters_out,
-                 double *resid_out, double *energy_out, const LaunchEnv &env) {
+                 double *resid_out, double *energy_out, int sx_fp64, const LaunchEnv &env) {
     const int P = pr.P;
     const int64_t rows = 2 * n;
     const int nchunks = chunks_for(rows, P, env.num_sms);
@@ -856,8 +859,9 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     const dim3 dgrid(dcb, nch_df);
 
     energy_kernel<<<1, kVecThreads, 0, s>>>(eloc, n, y, sc);
-    gemv_cols_split_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, Pp, chunk_rows, zpart, Oh, Ol, sc);
-    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, part, pf);
+    if (sx_fp64) gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
+    else gemv_cols_split_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, Pp, chunk_rows, zpart, Oh, Ol, sc);
+    cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, part, sx_fp64 ? nullptr : pf);
     cg_init_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
     if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR setup launch failed"; return NQS_ERR_CUDA; }
     *env.launches += 4;
@@ -870,12 +874,18 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
     int batch = iters_out && *iters_out > 0 ? std::min(std::max(*iters_out + 2, 4), 64) : 4;
     while (max_iter > 0) {
         for (int b = 0; b < batch; ++b) {
-            gemv_rows_df_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(Oh, Ol, pf, rows, Pp, y, ypart, sc);
-            center_df_kernel<<<cgb, kPvThreads, 0, s>>>(y, n, ypart, rgrid, yf, sc);
-            gemv_cols_df_kernel<<<dgrid, kColThreads, 0, s>>>(Oh, Ol, yf, rows, P, Pp, chunk_df, zpart, sc);
-            cg_ap_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nch_df, P, n, eps, p, Ap, part, sc);
+            if (sx_fp64) {
+                gemv_rows_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(O, p, rows, P, y, sc);
+                center_kernel<<<1, kVecThreads, 0, s>>>(y, n, sc);
+                gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
+            } else {
+                gemv_rows_df_kernel<<<rgrid, kRowWarps * 32, 0, s>>>(Oh, Ol, pf, rows, Pp, y, ypart, sc);
+                center_df_kernel<<<cgb, kPvThreads, 0, s>>>(y, n, ypart, rgrid, yf, sc);
+                gemv_cols_df_kernel<<<dgrid, kColThreads, 0, s>>>(Oh, Ol, yf, rows, P, Pp, chunk_df, zpart, sc);
+            }
+            cg_ap_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, sx_fp64 ? nchunks : nch_df, P, n, eps, p, Ap, part, sc);
             cg_xr_kernel<<<pvb, kPvThreads, 0, s>>>(P, p, Ap, delta, r, part, part2, sc);
-            cg_dir_kernel<<<pvb, kPvThreads, 0, s>>>(P, r, p, part2, sc, pf);
+            cg_dir_kernel<<<pvb, kPvThreads, 0, s>>>(P, r, p, part2, sc, sx_fp64 ? nullptr : pf);
             cg_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, rtol, max_iter, part2, sc);
         }
         done_iters += batch;

@@ -21,13 +21,14 @@ STATUS = {0: 'NQS_OK', -1: 'NQS_ERR_INVALID_ARG', -2: 'NQS_ERR_OOM', -3: 'NQS_ER
 NQS_ERR_NOT_CONVERGED = -5
 NQS_ERR_UNSUPPORTED = -7
 PRECISION = {'fp64': 0, 'fp32': 1, 'bf16': 2, 'fp8': 3}
+SX_ARITHMETIC = {'double_float': 0, 'fp64': 1}
 MODEL = {'j1j2': 0, 'tj': 1}
 
 EXPORTS = ('nqs_param_count', 'nqs_init', 'nqs_destroy', 'nqs_last_error', 'nqs_sync', 'nqs_kernel_launches',
            'nqs_logpsi',
            'nqs_connected', 'nqs_local_energy', 'nqs_local_energy_multi', 'nqs_sample', 'nqs_get_chains', 'nqs_set_chains',
            'nqs_logpsi_grad', 'nqs_logpsi_vjp', 'nqs_logpsi_grad_noalloc', 'nqs_noalloc_last_error', 'nqs_sr_solve',
-           'nqs_sr_solve_woodbury', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_probe_bounds', 'nqs_set_sm_limit',
+           'nqs_sr_solve_woodbury', 'nqs_set_sx_arithmetic', 'nqs_tc_plan', 'nqs_probe_wait_timeout', 'nqs_probe_bounds', 'nqs_set_sm_limit',
            'nqs_sampler_counts')
 
 
@@ -86,6 +87,7 @@ def load(path=None):
                                         ctypes.POINTER(D), I32]),
         'nqs_sr_solve_woodbury': (ctypes.c_int, [P, P, P, I64, D, D, I32, P, ctypes.POINTER(D), ctypes.POINTER(D),
                                                  I32]),
+        'nqs_set_sx_arithmetic': (ctypes.c_int, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -353,6 +355,10 @@ class Context:
                                                    ctypes.cast(energy, ctypes.POINTER(ctypes.c_double)),
                                                    int(bool(apply_update))))
         return delta, {'resid': resid.value, 'energy': complex(energy[0], energy[1])}
+
+    def set_sx_arithmetic(self, mode):
+        """nqs_set_sx_arithmetic: 'double_float' (default) or 'fp64' S.x passes in later sr_solve calls."""
+        self._check(self.lib.nqs_set_sx_arithmetic(self.ctx, SX_ARITHMETIC[mode]))
 
     def sr_solve(self, O, eloc, eps=1e-4, rtol=1e-8, max_iter=10000, lr=0.02, apply_update=False, delta=None):
         n = eloc.shape[0]

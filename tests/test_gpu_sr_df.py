@@ -41,10 +41,13 @@ NETS = [('silu', 4), ('silu', 8), ('cnn1', 4), ('cnn1', 8)]
 
 @pytest.mark.parametrize('net,channels', NETS)
 @pytest.mark.parametrize('as_float', [True, False])
-def test_cg_matches_dense_solve_float_planes(net, channels, as_float):
+@pytest.mark.parametrize('arith', ['double_float', 'fp64'])
+def test_cg_matches_dense_solve_float_planes(net, channels, as_float, arith):
     """Float-exact O (the float plane alone) and full float64 O (both planes);
-    P = 0 and 1 mod 4 (plane rows padded by 0 and 3 columns)."""
+    P = 0 and 1 mod 4 (plane rows padded by 0 and 3 columns); and the same
+    systems with the float64 passes."""
     ctx = _ctx(net, channels)
+    ctx.set_sx_arithmetic(arith)
     P, n = ctx.P, 300
     dA, dPhi, e = _system(P, n, 40 + channels + len(net), as_float)
     O = dev(np.concatenate([dA, dPhi], 0))
@@ -80,4 +83,24 @@ def test_float_planes_at_bench_size():
     got, info = ctx.sr_solve(O, E, eps=1e-4, rtol=1e-11, max_iter=10000)
     assert info['converged'] and info['resid'] <= 1e-11
     assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-8 * np.linalg.norm(want)
+    ctx.close()
+
+
+def test_double_float_and_fp64_passes_agree():
+    """Full float64 O at the 10x10 network's P: the two arithmetics' deltas
+    (both solved to rtol 1e-11) within 1e-9 of each other, and an unknown
+    mode refused."""
+    w = WL['j1j2_10x10']
+    ctx, _ = make_ctx(w)
+    P, n = ctx.P, 1024
+    dA, dPhi, e = _system(P, n, 17, False)
+    O = dev(np.concatenate([dA, dPhi], 0))
+    E = dev(np.stack([e.real, e.imag], 1))
+    d_df, i_df = ctx.sr_solve(O, E, eps=1e-4, rtol=1e-11, max_iter=10000)
+    ctx.set_sx_arithmetic('fp64')
+    d_64, i_64 = ctx.sr_solve(O, E, eps=1e-4, rtol=1e-11, max_iter=10000)
+    assert i_df['converged'] and i_64['converged']
+    assert torch.linalg.norm(d_df - d_64) <= 1e-9 * torch.linalg.norm(d_64)
+    assert i_df['energy'] == i_64['energy']
+    assert ctx.lib.nqs_set_sx_arithmetic(ctx.ctx, 7) == -1   # NQS_ERR_INVALID_ARG
     ctx.close()
