@@ -332,8 +332,12 @@ const char *nqs_noalloc_last_error(void);
  * float32 pipes, reading only the high plane when every low part is zero.
  * The force, every vector and scalar of the iteration and every row or
  * column total stay float64. Needs 8 bytes per element of O more working
- * memory (the two planes). NQS_SX_FP64: both passes in float64 FMAs on the
- * float64 O itself (GB300's float64 FMA rate bounds them). */
+ * memory (the two planes). Its values must stay in the float range: an
+ * element of O of magnitude 2^128 or more, or a product or partial sum
+ * beyond about 3.4e38, ends the solve with NQS_ERR_NONFINITE (parameters
+ * unchanged), and elements below 2^-80 count as zero. NQS_SX_FP64: both
+ * passes in float64 FMAs on the float64 O itself (float64 range; GB300's
+ * float64 FMA rate bounds them). */
 typedef enum { NQS_SX_DOUBLE_FLOAT = 0, NQS_SX_FP64 = 1 } nqs_sx_arithmetic;
 
 /* Select the S.x arithmetic of ctx's later nqs_sr_solve calls. Returns

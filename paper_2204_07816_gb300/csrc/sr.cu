@@ -458,7 +458,10 @@ __global__ void __launch_bounds__(kPvThreads) cg_ap_kernel(const double *zpart, 
     if (k < P) {
         double z = 0.0;
         for (int c = 0; c < nchunks; ++c) z += zpart[(int64_t)c * P + k];
-        const double a = z / (double)n + eps * p[k];
+        double a = z / (double)n + eps * p[k];
+        // an S.x product out of range (the double-float passes overflow past the float range, about 3.4e38) must
+        // not pass as a step: Inf becomes NaN, which reaches alpha, the residual and the non-finite status
+        if (!isfinite(a)) a = __longlong_as_double(0x7ff8000000000000LL);
         Ap[k] = a;
         pap = p[k] * a;
     }

@@ -104,3 +104,49 @@ def test_double_float_and_fp64_passes_agree():
     assert i_df['energy'] == i_64['energy']
     assert ctx.lib.nqs_set_sx_arithmetic(ctx.ctx, 7) == -1   # NQS_ERR_INVALID_ARG
     ctx.close()
+
+
+def test_split_edge_magnitudes():
+    """Elements the split treats specially: exact zero columns and magnitudes
+    below 2^-80 (taken as zero; their products are below 1e-24 of the O(1)
+    terms), against the oracle's dense solve in float64."""
+    ctx = _ctx('silu', 4)
+    P, n = ctx.P, 256
+    dA, dPhi, e = _system(P, n, 77, False)
+    rng = np.random.default_rng(78)
+    dA[:, :3] = 0.0                                   # whole zero columns
+    mask = rng.random(size=dA.shape) < 0.05
+    dA[mask] *= 1e-30                                 # tiny elements
+    O = dev(np.concatenate([dA, dPhi], 0))
+    E = dev(np.stack([e.real, e.imag], 1))
+    want, em = sr.solve_dense(dA, dPhi, e, 1e-3)
+    got, info = ctx.sr_solve(O, E, eps=1e-3, rtol=1e-12, max_iter=20000)
+    assert info['converged']
+    assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-8 * np.linalg.norm(want)
+    ctx.close()
+
+
+def test_products_beyond_float_range():
+    """O scaled by 1e20: the double-float passes' sums leave the float range,
+    which the solve reports as NQS_ERR_NONFINITE (parameters unchanged), while
+    the float64 passes solve the same system (eps scaled with S)."""
+    nqs = lib()
+    ctx = _ctx('silu', 4)
+    P, n = ctx.P, 128
+    dA, dPhi, e = _system(P, n, 79, False)
+    dA *= 1e20
+    dPhi *= 1e20
+    eps = 1e-3 * 1e40
+    O = dev(np.concatenate([dA, dPhi], 0))
+    E = dev(np.stack([e.real, e.imag], 1))
+    before = ctx.params.clone()
+    with pytest.raises(nqs.NQSError) as ex:
+        ctx.sr_solve(O, E, eps=eps, rtol=1e-12, max_iter=2000, lr=0.1, apply_update=True)
+    assert ex.value.code == -4, ex.value   # NQS_ERR_NONFINITE
+    assert torch.equal(ctx.params, before)
+    ctx.set_sx_arithmetic('fp64')
+    want, _ = sr.solve_dense(dA, dPhi, e, eps)
+    got, info = ctx.sr_solve(O, E, eps=eps, rtol=1e-12, max_iter=20000)
+    assert info['converged']
+    assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-8 * np.linalg.norm(want)
+    ctx.close()
