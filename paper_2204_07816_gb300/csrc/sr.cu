@@ -1,10 +1,12 @@
-// Stochastic reconfiguration solve in float64 (Sec. 3.2; Sec. 5.4.1
-// "Distributed SR computation"). The paper builds the covariance matrix
-// S explicitly and factorises it; here S is never formed:
+// Stochastic reconfiguration solve (Sec. 3.2; Sec. 5.4.1 "Distributed SR
+// computation"). The paper builds the covariance matrix S explicitly and
+// factorises it; here S is never formed:
 //   (S + eps I) x = Ohat^T (Ohat x - mean) / n + eps x
 // with Ohat the real-stacked [2n, P] matrix of local derivatives, and the
-// system is solved by conjugate gradient. Every reduction runs in a fixed
-// order, so results do not depend on what else runs on the GPU.
+// system is solved by conjugate gradient, its vectors and scalars in
+// float64 and its two passes over O per iteration in double-float (default)
+// or float64 arithmetic (below). Every reduction runs in a fixed order, so
+// results do not depend on what else runs on the GPU.
 //
 // Sample-space form (run_sr_woodbury): the same delta is
 //   delta = Ohat^T y,   (Ohat Ohat^T / n + eps I) y = Ehat / n,
