@@ -117,9 +117,10 @@ __global__ void __launch_bounds__(kRowWarps * 32) gemv_rows_kernel(const double 
 // element, the l * l term is dropped) and every accumulation is a
 // renormalised double-float add, so a dot product's error stays near 1e-15 of
 // the sum of its terms' magnitudes (float64: about 1e-17). Where every
-// element of O is a float (the float32 and bf16 local derivatives are), the l
-// plane is all zero: the split pass records whether any l is not, and the
-// passes then read the h plane alone, half the bytes, with the same results.
+// element of O is a float (the float32 and bf16 local derivatives are), every
+// l is zero: the split pass records whether any l is not, the l plane is
+// written (by a second pass over O) only then, and otherwise the passes read
+// the h plane alone, half the bytes, with the same results.
 
 // a + b, both double-floats: two-sum of the high parts, then renormalised.
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
@@ -162,14 +163,14 @@ __device__ __forceinline__ float2 df_split_bits(uint2 w) {
 
 // The force pass: zpart[chunk][k] = sum over the chunk's rows r of O[r, k] y[r]
 // in float64, in gemv_cols_kernel's order (the same sums), and every element
-// of O split into the planes Oh and Ol (row stride Pp = P rounded up to a
-// multiple of 4, the pad columns zero); sc[S_WIDE] = 1 if any l is not zero.
+// of O split into h + l with h written to the plane Oh (row stride Pp = P
+// rounded up to a multiple of 4, the pad columns zero); sc[S_WIDE] = 1 if any
+// l is not zero, and split_low_kernel then writes the l plane.
 __global__ void __launch_bounds__(kColThreads) gemv_cols_split_kernel(const double *__restrict__ O,
                                                                       const double *__restrict__ y, int64_t rows, int P,
                                                                       int Pp, int64_t chunk_rows,
                                                                       double *__restrict__ zpart,
-                                                                      float *__restrict__ Oh, float *__restrict__ Ol,
-                                                                      double *sc) {
+                                                                      float *__restrict__ Oh, double *sc) {
     if (sc[S_DONE] != 0.0) return;
     const int k = blockIdx.x * kColThreads + threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * chunk_rows;
@@ -187,7 +188,6 @@ __global__ void __launch_bounds__(kColThreads) gemv_cols_split_kernel(const doub
             for (int u = 0; u < 4; ++u) {
                 const float2 d = df_split_bits(w[u]);
                 __stcs(Oh + (r + u) * Pp + k, d.x);
-                __stcs(Ol + (r + u) * Pp + k, d.y);
                 wide |= d.y != 0.f;
             }
             a0 = fma(__hiloint2double((int)w[0].y, (int)w[0].x), y[r], a0);
@@ -199,16 +199,28 @@ __global__ void __launch_bounds__(kColThreads) gemv_cols_split_kernel(const doub
             const uint2 w = __ldcs(col + r * P);
             const float2 d = df_split_bits(w);
             __stcs(Oh + r * Pp + k, d.x);
-            __stcs(Ol + r * Pp + k, d.y);
             wide |= d.y != 0.f;
             a0 = fma(__hiloint2double((int)w.y, (int)w.x), y[r], a0);
         }
         zpart[(int64_t)blockIdx.y * P + k] = (a0 + a1) + (a2 + a3);
     } else if (k < Pp) {
-        for (int64_t r = r0; r < r1; ++r) { Oh[r * Pp + k] = 0.f; Ol[r * Pp + k] = 0.f; }
+        for (int64_t r = r0; r < r1; ++r) Oh[r * Pp + k] = 0.f;
     }
     // the same value from every writer
     if (__any_sync(0xffffffffu, wide) && (threadIdx.x & 31) == 0) sc[S_WIDE] = 1.0;
+}
+
+// The l plane, only when the force pass found an l that is not zero (O not
+// made of floats): every element split again, the pad columns zero. Rows
+// r = blockIdx.y, blockIdx.y + gridDim.y, ...
+__global__ void __launch_bounds__(kColThreads) split_low_kernel(const double *__restrict__ O, int64_t rows, int P,
+                                                                int Pp, float *__restrict__ Ol, const double *sc) {
+    if (sc[S_DONE] != 0.0 || sc[S_WIDE] == 0.0) return;
+    const int k = blockIdx.x * kColThreads + threadIdx.x;
+    if (k >= Pp) return;
+    const uint2 *col = reinterpret_cast<const uint2 *>(O) + k;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y)
+        __stcs(Ol + r * Pp + k, k < P ? df_split_bits(__ldcs(col + r * P)).y : 0.f);
 }
 
 // acc[j] += x[j] q[j] for the four columns of a float4 group (l parts zero
@@ -865,11 +877,15 @@ int run_sr_solve(const Problem &pr, const double *O, const double *eloc, int64_t
 
     energy_kernel<<<1, kVecThreads, 0, s>>>(eloc, n, y, sc);
     if (sx_fp64) gemv_cols_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, chunk_rows, zpart, sc);
-    else gemv_cols_split_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, Pp, chunk_rows, zpart, Oh, Ol, sc);
+    else {
+        gemv_cols_split_kernel<<<cgrid, kColThreads, 0, s>>>(O, y, rows, P, Pp, chunk_rows, zpart, Oh, sc);
+        split_low_kernel<<<dim3((Pp + kColThreads - 1) / kColThreads, (unsigned)std::min<int64_t>(rows, 1024)),
+                           kColThreads, 0, s>>>(O, rows, P, Pp, Ol, sc);
+    }
     cg_init_kernel<<<pvb, kPvThreads, 0, s>>>(zpart, nchunks, P, n, delta, r, p, part, sx_fp64 ? nullptr : pf);
     cg_init_scalars_kernel<<<1, kPvThreads, 0, s>>>(pvb, part, sc);
     if (cudaGetLastError() != cudaSuccess) { *env.msg = "SR setup launch failed"; return NQS_ERR_CUDA; }
-    *env.launches += 4;
+    *env.launches += sx_fp64 ? 4 : 5;
 
     double host_sc[S_COUNT];
     int done_iters = 0;

@@ -150,3 +150,21 @@ def test_products_beyond_float_range():
     assert info['converged']
     assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-8 * np.linalg.norm(want)
     ctx.close()
+
+
+@pytest.mark.parametrize('n', [1, 3, 9])
+@pytest.mark.parametrize('as_float', [True, False])
+def test_few_samples(n, as_float):
+    """Ragged row blocks of the passes (2n = 2, 6, 18 rows against blocks of 8
+    rows) and P = 1 mod 4, against the oracle's dense solve."""
+    ctx = _ctx('cnn1', 4)
+    P = ctx.P
+    dA, dPhi, e = _system(P, n, 200 + n, as_float)
+    O = dev(np.concatenate([dA, dPhi], 0))
+    E = dev(np.stack([e.real, e.imag], 1))
+    want, em = sr.solve_dense(dA, dPhi, e, 1e-2)
+    got, info = ctx.sr_solve(O, E, eps=1e-2, rtol=1e-12, max_iter=10000)
+    assert info['converged']
+    assert np.linalg.norm(got.cpu().numpy() - want) <= 1e-9 * max(np.linalg.norm(want), 1e-300)
+    assert abs(info['energy'] - em) <= 1e-12 * abs(em)
+    ctx.close()
