@@ -29,14 +29,20 @@ def test_logpsi_grad_full_network(prec, tol):
     assert rel_err(O[3:], dPhi) <= tol
 
 
-def test_sr_solves_at_full_parameter_count():
+@pytest.mark.parametrize('as_float', [False, True])
+def test_sr_solves_at_full_parameter_count(as_float):
     """CG (parameter space) and the sample-space Cholesky solve on the GPU
-    against the oracle's sample-space solve, P = 65,120 and 256 samples."""
+    against the oracle's sample-space solve, P = 65,120 and 256 samples; O
+    in full float64 (both planes of the CG's double-float split) and made of
+    floats (the float plane alone, as the bf16 local derivatives are)."""
     ctx, _ = make_ctx(W16)
     P, n = ctx.P, 256
     rng = np.random.default_rng(83)
     dA = rng.normal(size=(n, P)) + rng.normal(size=P)
     dPhi = 0.5 * rng.normal(size=(n, P))
+    if as_float:
+        dA = dA.astype(np.float32).astype(np.float64)
+        dPhi = dPhi.astype(np.float32).astype(np.float64)
     e = -300.0 + rng.normal(size=n) + 0.2j * rng.normal(size=n)
     O = dev(np.concatenate([dA, dPhi], 0))
     E = dev(np.stack([e.real, e.imag], 1))
