@@ -14,7 +14,7 @@ The paper describes them in words only (its figure is not available):
   neurons to the end; a final convolution reduces the channels to one and the
   coefficient is the product of its neurons.
 
-Reading fixed for this build (the paper gives no sizes; the operator table of
+Reading taken here (the paper gives no sizes; the operator table of
 Sec. 5.4.2 shows activations as [batch, sites, channels] with a 10 x 10
 lattice padded to 12 x 12, so the one-dimensional operators run over the
 row-major site order s = y L + x):
