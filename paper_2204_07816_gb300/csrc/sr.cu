@@ -372,6 +372,74 @@ __device__ __forceinline__ void cols_df(const float *__restrict__ Oh, const floa
         if (4 * c4 + j < P) zpart[(int64_t)blockIdx.y * P + 4 * c4 + j] = df_value(acc[j]);
 }
 
+// The column pass's float-plane form with Blackwell's packed float32
+// instructions (add / mul / fma .f32x2): the four columns' accumulators as
+// two pairs of double-floats (S01, C01), (S23, C23), each lane the same IEEE
+// operation as df_fma's, so every sum is bitwise cols_df<false, U>'s with
+// half the float32 instructions. a - b is formed as fma(b, -1, a) (one
+// rounding of the exact difference, as the subtraction).
+__device__ __forceinline__ float2 df_sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void df_fma_pair(float2 &S, float2 &C, float2 h, float2 qh, float2 ql) {
+    const float2 p = __fmul2_rn(h, qh);
+    float2 e = __ffma2_rn(h, qh, __fmul2_rn(p, make_float2(-1.f, -1.f)));
+    e = __ffma2_rn(h, ql, e);
+    const float2 sum = __fadd2_rn(S, p);
+    const float2 bb = df_sub2(sum, S);
+    const float2 t = __fadd2_rn(df_sub2(S, df_sub2(sum, bb)), df_sub2(p, bb));
+    const float2 u = __fadd2_rn(t, __fadd2_rn(C, e));
+    const float2 hi = __fadd2_rn(sum, u);
+    C = df_sub2(u, df_sub2(hi, sum));
+    S = hi;
+}
+
+template <int U>
+__device__ __forceinline__ void cols_df_packed(const float *__restrict__ Oh, const float2 *__restrict__ y,
+                                               int64_t rows, int P, int Pp, int64_t chunk_rows, int c4,
+                                               double *__restrict__ zpart) {
+    const int64_t r0 = (int64_t)blockIdx.y * chunk_rows;
+    const int64_t r1 = rows < r0 + chunk_rows ? rows : r0 + chunk_rows;
+    const int64_t s4 = Pp >> 2;
+    const float4 *ch = reinterpret_cast<const float4 *>(Oh) + c4;
+    float2 S01 = make_float2(0.f, 0.f), C01 = S01, S23 = S01, C23 = S01;
+    int64_t r = r0;
+    float4 oh[U];
+    if (r + U - 1 < r1) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) oh[u] = __ldcs(ch + (r + u) * s4);
+    }
+    while (r + U - 1 < r1) {
+        const int64_t rn = r + U;
+        const bool more = rn + U - 1 < r1;
+        float4 nh[U];
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) nh[u] = __ldcs(ch + (rn + u) * s4);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float2 q = y[r + u];
+            const float2 qh = make_float2(q.x, q.x), ql = make_float2(q.y, q.y);
+            df_fma_pair(S01, C01, make_float2(oh[u].x, oh[u].y), qh, ql);
+            df_fma_pair(S23, C23, make_float2(oh[u].z, oh[u].w), qh, ql);
+        }
+        r = rn;
+        if (!more) break;
+#pragma unroll
+        for (int u = 0; u < U; ++u) oh[u] = nh[u];
+    }
+    for (; r < r1; ++r) {
+        const float2 q = y[r];
+        const float4 o = __ldcs(ch + r * s4);
+        df_fma_pair(S01, C01, make_float2(o.x, o.y), make_float2(q.x, q.x), make_float2(q.y, q.y));
+        df_fma_pair(S23, C23, make_float2(o.z, o.w), make_float2(q.x, q.x), make_float2(q.y, q.y));
+    }
+    const float2 a[4] = {make_float2(S01.x, C01.x), make_float2(S01.y, C01.y), make_float2(S23.x, C23.x),
+                         make_float2(S23.y, C23.y)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (4 * c4 + j < P) zpart[(int64_t)blockIdx.y * P + 4 * c4 + j] = df_value(a[j]);
+}
+
 __global__ void __launch_bounds__(kColThreads) gemv_cols_df_kernel(const float *__restrict__ Oh,
                                                                    const float *__restrict__ Ol,
                                                                    const float2 *__restrict__ y, int64_t rows, int P,
@@ -381,7 +449,7 @@ __global__ void __launch_bounds__(kColThreads) gemv_cols_df_kernel(const float *
     const int c4 = blockIdx.x * kColThreads + threadIdx.x;
     if (c4 >= (Pp >> 2)) return;
     if (sc[S_WIDE] != 0.0) cols_df<true, 4>(Oh, Ol, y, rows, P, Pp, chunk_rows, c4, zpart);
-    else cols_df<false, 16>(Oh, Ol, y, rows, P, Pp, chunk_rows, c4, zpart);
+    else cols_df_packed<8>(Oh, y, rows, P, Pp, chunk_rows, c4, zpart);
 }
 
 // Subtract the mean of each half of y (real rows, imaginary rows).
